@@ -1,0 +1,148 @@
+/*
+ * npf.h -- C ABI of the GB300 library for high-order nonlinear participation factors (NPFs).
+ *
+ * Method: arXiv 2509.08968 (Sajjadi, Huang, Sun), Section II. For every Taylor order N the
+ * library forms the modal tensor
+ *
+ *     h^i_{p_1..p_N} = (1/N!) sum_j sum_{a_1..a_N} psi_{ij} A_N^j_{a_1..a_N} phi_{a_1 p_1}..phi_{a_N p_N}
+ *                      / (lambda_{p_1} + .. + lambda_{p_N} - lambda_i)                    (Eq. 4)
+ *
+ * by the contraction chain of Algorithm 2 (steps 1-11: every lower index with Phi, the upper index
+ * with Psi, the factor 1/N!, the resonance denominators with the clamp |D| < eps -> eps), reduces
+ * it with the left-eigenvector components into
+ *
+ *     Psi_N[i,k] = - sum_{p_1..p_N} h^i_{p_1..p_N} psi_{p_1 k} .. psi_{p_N k}   (Alg. 2 steps 12-19,
+ *                                                                              Eq. 7, zeta = Psi[:,k])
+ * and returns
+ *
+ *     NPF[k,i] = phi_{k i} (psi_{i k} + sum_{N=2..order} Psi_N[i,k])          (Alg. 2 step 20)
+ *
+ * (the product of step 20 read elementwise; order 1 gives the linear participation factors).
+ *
+ * Conventions
+ *   - Complex numbers are interleaved (re, im) doubles: npf_c128.
+ *   - U[a*n + p]  = phi_{a p}: column p is the right eigenvector of mode p (row-major n x n).
+ *   - V[i*n + k]  = psi_{i k}: row i is the left eigenvector of mode i; V must equal U^-1.
+ *   - Packed tensor of order N: coeffs[j*P + r] = A_N^j_{a_1..a_N} (the N-th derivative tensor,
+ *     symmetric in its lower indices) for the r-th non-decreasing tuple a_1 <= .. <= a_N in
+ *     lexicographic order, P = C(n+N-1, N). The library applies the 1/N! of Algorithm 2 step 4.
+ *   - Outputs are row-major n x n: out[k*n + i] = NPF(state k, mode i).
+ *   - Pointers may be host or device memory (classified with cudaPointerGetAttributes); the
+ *     caller owns every pointer it passes. npf_plan and npf_set_tensor copy their inputs.
+ *   - Every call returns NPF_OK or an error code and writes nothing to the outputs on error;
+ *     npf_last_error() gives a message (thread-local). No C++ exception crosses the ABI.
+ *   - A handle is used by one host thread at a time. Work is issued on the handle's stream
+ *     (NPF_OPT_STREAM), and every call returns after that stream has finished its work.
+ */
+#ifndef NPF_H_
+#define NPF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } npf_c128;
+typedef struct npf_handle npf_handle;
+
+enum npf_status {
+    NPF_OK = 0,
+    NPF_ERR_ARG = 1,             /* bad argument (size, order, pointer, option) */
+    NPF_ERR_NOT_INVERSE = 2,     /* max |V U - I| above NPF_INVERSE_TOL */
+    NPF_ERR_OOM = 3,             /* the memory budget or the device cannot hold the work set */
+    NPF_ERR_MISSING_TENSOR = 4,  /* npf_compute(order >= 2) before npf_set_tensor(order) */
+    NPF_ERR_CUDA = 5,            /* a CUDA runtime call failed; message in npf_last_error() */
+    NPF_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up */
+    NPF_ERR_UNSUPPORTED = 7      /* valid request this build does not implement (e.g. n > 128 on
+                                    the tensor-core path) */
+};
+
+/* Tolerance of the V U = I check in npf_plan (max-abs entry of V U - I). */
+#define NPF_INVERSE_TOL 1e-8
+
+/* Option keys for npf_set_option. */
+enum npf_option {
+    NPF_OPT_PRECISION = 0,  /* value: enum npf_precision. Default NPF_PREC_SPLIT_BF16. */
+    NPF_OPT_EPS = 1,        /* resonance clamp eps of Alg. 2 step 9 (default 1e-8; > 0). */
+    NPF_OPT_STREAM = 2,     /* cudaStream_t, passed as its integer value (0 = legacy default). */
+    NPF_OPT_SLICES = 3,     /* BF16 slices per operand on the split paths (2..6). Defaults: 5 for
+                               NPF_PREC_SPLIT_BF16, 3 for NPF_PREC_FP32. */
+    NPF_OPT_DIVIDE = 4,     /* 1 (default): divide by the resonance denominators. 0: D = 1, a
+                               debugging switch behind the collapse identity
+                               sum_p C^i_p prod_m psi_{p_m k} = (1/N!) sum_j psi_ij A^j_{k..k}. */
+    NPF_OPT_MEM_BUDGET = 5, /* bytes of device memory for intermediates; 0 = 80% of free memory. */
+    NPF_OPT_PROFILE = 6     /* 1: time each kernel launch with CUDA events (npf_get_profile). */
+};
+
+/* Arithmetic of the dense contraction. The denominators, the divide, the Psi_N sums and the
+ * NPF finish are native FP64 in every form. */
+enum npf_precision {
+    NPF_PREC_FP64 = 0,        /* native FP64 (CUDA-core DFMA) contraction */
+    NPF_PREC_SPLIT_BF16 = 1,  /* FP64-emulating BF16 slices on tcgen05 tensor cores, FP32
+                                 accumulation in TMEM, exact fixed-point recombination */
+    NPF_PREC_FP32 = 2         /* the same tensor-core kernels with 3 slices (FP32-level error) */
+};
+
+/* Create a plan for an n-state system with Taylor orders up to N_max (1..6).
+ * eigvals[n], U[n*n], V[n*n] (layouts above; host or device). mem_budget: bytes of device memory
+ * the intermediates may use, 0 = 80% of the free device memory at plan time (sizing rule of
+ * Algorithm 1 applied to the output index space). Checks max|V U - I| <= NPF_INVERSE_TOL.
+ * Returns NULL on error (npf_last_error() tells why; npf_last_status() gives the code). */
+npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* U,
+                     const npf_c128* V, size_t mem_budget);
+
+/* Copy the packed order-`order` tensor (2 <= order <= N_max; layout above; host or device) into
+ * the plan's device memory. Replaces a previous tensor of that order. */
+int npf_set_tensor(npf_handle* h, int order, const double* coeffs);
+
+/* NPF of the given order (1..N_max) into out[n*n] (host or device): linear PFs plus Psi_m of
+ * every order 2..order that has a tensor set (each order is an independent approximation, Eq. 4).
+ * Returns NPF_ERR_MISSING_TENSOR only when order >= 2 and that order's own tensor is missing. */
+int npf_compute(npf_handle* h, int order, npf_c128* out);
+
+/* Release every device and host resource of the plan. NULL is a no-op. */
+void npf_destroy(npf_handle* h);
+
+/* Set an option (keys above). */
+int npf_set_option(npf_handle* h, int key, double value);
+
+/* The order-only term Psi_N (out[i*n + k], host or device), recomputed by this call. */
+int npf_get_term(npf_handle* h, int order, npf_c128* out);
+
+/* One modal slab h^i_{prefix, q}: out[i*n + q] for the fixed prefix p_1..p_{N-1} (N-1 ints in
+ * [0, n)), every mode i and last index q. Host or device `out`. For parity checks at full size. */
+int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* out);
+
+/* Many plans in one call (independent systems of uneven size and order): computes
+ * NPF_{orders[b]} of plans[b] into outs[b] for b < count. Work of all systems is issued as one
+ * captured CUDA graph on the first plan's stream. */
+int npf_batch_compute(int count, npf_handle* const* plans, const int* orders,
+                      npf_c128* const* outs);
+
+/* Message / code of the last error raised on this host thread. */
+const char* npf_last_error(void);
+int npf_last_status(void);
+
+/* Algorithm 1 (Section II.B) batch sizing, host-only arithmetic: a tensor with n_dim dimensions
+ * of size n_s and `bytes` bytes per element, memory limit m_limit_gb (GiB, 1024^-3). Writes the
+ * batch count per dimension BC[n_dim] and the largest batch shape max_batch[n_dim], and the total
+ * and per-batch sizes in GiB. Returns the number of batches (prod BC), or -1 on bad arguments. */
+int64_t npf_alg1_batches(int n_dim, int n_s, double m_limit_gb, int bytes, int64_t* BC,
+                         int64_t* max_batch, double* total_gb, double* per_batch_gb);
+
+/* Per-kernel timing recorded while NPF_OPT_PROFILE is 1: fills up to `cap` entries with the
+ * kernel name (static string), launch count and total milliseconds (CUDA events on the handle's
+ * stream); returns the number of distinct kernels. Reset with reset != 0. */
+int npf_get_profile(npf_handle* h, int cap, const char** names, int64_t* launches, double* ms,
+                    int reset);
+
+/* Number of kernels this library has launched in the process so far (all handles). */
+int64_t npf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NPF_H_ */
