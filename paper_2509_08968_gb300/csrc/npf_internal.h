@@ -1,0 +1,126 @@
+// npf_internal.h -- internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/npf.h"
+
+namespace npf {
+
+constexpr int kMaxOrder = 6;
+constexpr int kMaxN = 4096;
+
+// ----------------------------------------------------------------------------------------
+// Errors: a failing step throws npf::Error inside the library; every ABI entry point catches
+// it, records the message thread-locally and returns the code.
+// ----------------------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define NPF_CUDA(x) ::npf::check_cuda((x), #x)
+
+// ----------------------------------------------------------------------------------------
+// Kernel profiling / launch counting.
+// ----------------------------------------------------------------------------------------
+struct Profiler {
+    bool enabled = false;
+    struct Rec { int64_t launches = 0; double ms = 0.0; };
+    std::map<std::string, Rec> recs;
+    std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    void begin(const char* name, cudaStream_t s, cudaEvent_t* e0);
+    void end(const char* name, cudaStream_t s, cudaEvent_t e0);
+    void flush();  // after a stream sync: accumulate pending event pairs
+};
+void note_launch();  // one more kernel launched by this library
+
+// RAII launch bracket: times the launch when profiling is on and counts it.
+struct LaunchScope {
+    Profiler* p;
+    const char* name;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr;
+    LaunchScope(Profiler* p_, const char* n_, cudaStream_t s_);
+    ~LaunchScope();
+};
+
+// ----------------------------------------------------------------------------------------
+// Device scratch arena (grows on demand, bounded by the plan's budget).
+// ----------------------------------------------------------------------------------------
+struct Arena {
+    void* base = nullptr;
+    size_t cap = 0;
+    void reserve(size_t bytes);
+    void release();
+};
+
+struct SplitOperand;  // per-precision prepared matrices (defined in the split unit)
+
+// ----------------------------------------------------------------------------------------
+// The plan.
+// ----------------------------------------------------------------------------------------
+struct Plan {
+    int n = 0, Nmax = 0;
+    int precision = NPF_PREC_SPLIT_BF16;
+    int slices = 0;                // 0 = default for the precision
+    double eps = 1e-8;
+    int divide = 1;
+    size_t mem_budget = 0;         // 0 = 80% of free memory at compute time
+    cudaStream_t stream = nullptr;
+    Profiler prof;
+
+    // device copies of the inputs (interleaved complex doubles)
+    double2* d_lam = nullptr;
+    double2* d_U = nullptr;        // phi_{a p} at a*n + p
+    double2* d_V = nullptr;        // psi_{i k} at i*n + k
+    double2* d_Vt = nullptr;       // psi_{i k} at k*n + i (transposed copy)
+    double* d_tensor[kMaxOrder + 1] = {};   // packed per order
+    int64_t packed_count[kMaxOrder + 1] = {};
+
+    // device tables
+    int64_t* d_cnt = nullptr;      // cnt[r*(n+1) + v] = #non-decreasing r-tuples in [v, n)
+
+    // results of the last compute
+    double2* d_psiN[kMaxOrder + 1] = {};   // Psi_N[i*n + k]
+    double2* d_npf = nullptr;
+    double2* d_sum = nullptr;
+
+    Arena arena;
+    SplitOperand* split = nullptr;
+};
+
+int64_t packed_count(int n, int N);
+int64_t ipow64(int64_t b, int e);
+
+// Resolve the memory budget (bytes) for intermediates.
+size_t effective_budget(const Plan& p);
+
+// ----------------------------------------------------------------------------------------
+// Native FP64 path (k_fp64.cu).
+// ----------------------------------------------------------------------------------------
+void fp64_term(Plan& p, int N, double2* d_out /* Psi_N [n][n] */);
+void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out /* h [n][n] */);
+
+// ----------------------------------------------------------------------------------------
+// Split BF16 tensor-core path (k_split.cu).
+// ----------------------------------------------------------------------------------------
+void split_term(Plan& p, int N, double2* d_out);
+void split_slab(Plan& p, int N, const int* prefix, double2* d_out);
+void split_release(Plan& p);
+
+// ----------------------------------------------------------------------------------------
+// Small shared kernels (k_common.cu).
+// ----------------------------------------------------------------------------------------
+void launch_finish(Plan& p, const double2* d_sum, double2* d_npf);   // NPF = phi o (psi + S)^T
+void launch_zero(Plan& p, double2* d, int64_t count);
+void launch_add(Plan& p, double2* acc, const double2* x, int64_t count);
+void build_cnt_table(Plan& p);
+
+}  // namespace npf
