@@ -67,7 +67,7 @@ enum npf_option {
     NPF_OPT_PRECISION = 0,  /* value: enum npf_precision. Default NPF_PREC_SPLIT_BF16. */
     NPF_OPT_EPS = 1,        /* resonance clamp eps of Alg. 2 step 9 (default 1e-8; > 0). */
     NPF_OPT_STREAM = 2,     /* cudaStream_t, passed as its integer value (0 = legacy default). */
-    NPF_OPT_SLICES = 3,     /* BF16 slices per operand on the split paths (2..6). Defaults: 5 for
+    NPF_OPT_SLICES = 3,     /* BF16 slices per operand on the split paths (2..6). Defaults: 6 for
                                NPF_PREC_SPLIT_BF16, 3 for NPF_PREC_FP32. */
     NPF_OPT_DIVIDE = 4,     /* 1 (default): divide by the resonance denominators. 0: D = 1, a
                                debugging switch behind the collapse identity

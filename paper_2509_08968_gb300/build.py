@@ -16,7 +16,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["npf_api.cu", "k_common.cu", "k_fp64.cu", "k_split.cu"]
-HEADERS = ["npf_internal.h", "k_device.cuh"]
+HEADERS = ["npf_internal.h", "k_device.cuh", "k_tc.cuh"]
 
 
 def _nvcc():

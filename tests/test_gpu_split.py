@@ -1,0 +1,147 @@
+"""Split-BF16 tensor-core path (and its FP32-level form) against the CPU oracle.
+
+Bars from the specification of the path: relative Frobenius error <= 1e-10 for the FP64-emulating
+split form (5 BF16 slices) and <= 1e-5 for the FP32 form (3 slices), for h slabs, Psi_N and NPF.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import npf_synth as S
+import oracle
+from tests._util import make_plan, rel_fro
+
+pytestmark = pytest.mark.gpu
+TOL = {"split_bf16": 1e-10, "fp32": 1e-5}
+# The collapse identity sums n^N modal terms that cancel to a single tensor entry (about four
+# orders of magnitude of cancellation at n = 60..120, N = 4), so a per-entry error e appears as
+# ~1e4 e in the collapsed result. It is a structural check at full size (a wrong index, sign or
+# factor gives an O(1) error); the 1e-10 bar is checked against the oracle directly.
+COLLAPSE_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def npf():
+    from paper_2509_08968_gb300 import build
+    build.build()
+    import paper_2509_08968_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_small_system(npf, prec, seed):
+    sysm = S.config_small(seed, orders=(2, 3))
+    with make_plan(npf, sysm, 3, prec) as p:
+        for N in (2, 3):
+            ref = oracle.psiN(sysm.tensors[N], 10, N, sysm.U, sysm.V, sysm.lam, p1_block=10)
+            err = rel_fro(p.term(N), ref)
+            assert err < TOL[prec], (N, err)
+        ref = oracle.npf_orders(sysm, 3, p1_block=10)
+        assert rel_fro(p.compute(3), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("n,N", [(6, 4), (10, 4)])
+def test_high_order_small_n(npf, n, N):
+    sysm = S.modal_system(n, 3 * n + N)
+    sysm.tensors[N] = S.random_packed_tensor(n, N, 17 + N)
+    with make_plan(npf, sysm, N, "split_bf16") as p:
+        ref = oracle.psiN(sysm.tensors[N], n, N, sysm.U, sysm.V, sysm.lam, p1_block=n)
+        assert rel_fro(p.term(N), ref) < 1e-10
+
+
+def test_slabs_small(npf):
+    sysm = S.config_small(3, orders=(3,))
+    with make_plan(npf, sysm, 3, "split_bf16") as p:
+        for pre in ([0, 0], [3, 7], [9, 2]):
+            ref = oracle.h_slab(sysm.tensors[3], 10, 3, sysm.U, sysm.V, sysm.lam, pre)
+            assert rel_fro(p.modal_slab(3, pre), ref) < 1e-10
+
+
+def test_multi_batch_equals_single(npf):
+    sysm = S.config_blocks(20, 5, orders=(3,))
+    ref = oracle.psiN(sysm.tensors[3], 20, 3, sysm.U, sysm.V, sysm.lam, p1_block=20)
+    with make_plan(npf, sysm, 3, "split_bf16") as p:
+        one = p.term(3)
+        p.set_option(npf.OPT_MEM_BUDGET, 400e6)
+        many = p.term(3)
+    assert rel_fro(one, ref) < 1e-10 and rel_fro(many, ref) < 1e-10
+
+
+def test_n60_order3_full(npf):
+    sysm = S.config_n60(0, orders=(3,))
+    ref = oracle.psiN(sysm.tensors[3], 60, 3, sysm.U, sysm.V, sysm.lam, p1_block=4)
+    for prec in ("split_bf16", "fp32"):
+        with make_plan(npf, sysm, 3, prec) as p:
+            assert rel_fro(p.term(3), ref) < TOL[prec]
+
+
+def test_order5_is_reported_unsupported(npf):
+    sysm = S.modal_system(4, 9)
+    sysm.tensors[5] = S.random_packed_tensor(4, 5, 1)
+    with make_plan(npf, sysm, 5, "split_bf16") as p:
+        with pytest.raises(npf.NpfError) as e:
+            p.term(5)
+        assert e.value.status == npf.NPF_ERR_UNSUPPORTED
+
+
+def test_n60_order4_slabs_and_collapse(npf):
+    sysm = S.config_n60(2, orders=(4,))
+    n, N = 60, 4
+    with make_plan(npf, sysm, 4, "split_bf16") as p:
+        rng = np.random.default_rng(1)
+        for _ in range(2):
+            pre = [int(x) for x in rng.integers(0, n, size=3)]
+            ref = oracle.h_slab(sysm.tensors[4], n, 4, sysm.U, sysm.V, sysm.lam, pre)
+            assert rel_fro(p.modal_slab(4, pre), ref) < 1e-10
+        p.set_option(npf.OPT_DIVIDE, 0)
+        diag = [S.packed_count(n, N) - S.packed_count(n - k, N) for k in range(n)]
+        expect = -(sysm.V @ sysm.tensors[N][:, diag]) / math.factorial(N)
+        assert rel_fro(p.term(N), expect) < COLLAPSE_TOL
+
+
+GOLD3 = os.path.join(os.path.dirname(__file__), "golden", "n120_seed0_order3.npz")
+
+
+@pytest.mark.skipif(not os.path.exists(GOLD3), reason="golden file not generated")
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_n120_order3_against_stored_oracle(npf, prec):
+    sysm = S.config_n120(0, orders=(3,))
+    ref = np.load(GOLD3)["psi3"]
+    with make_plan(npf, sysm, 3, prec) as p:
+        assert rel_fro(p.term(3), ref) < TOL[prec]
+
+
+def test_n120_order4_collapse_identity(npf):
+    """Full-size order-4 contraction (n = 120) checked by the collapse identity, divide off."""
+    sysm = S.config_n120(0, orders=(4,))
+    n, N = 120, 4
+    diag = [S.packed_count(n, N) - S.packed_count(n - k, N) for k in range(n)]
+    expect = -(sysm.V @ sysm.tensors[N][:, diag]) / math.factorial(N)
+    with make_plan(npf, sysm, 4, "split_bf16") as p:
+        p.set_option(npf.OPT_DIVIDE, 0)
+        assert rel_fro(p.term(N), expect) < COLLAPSE_TOL
+
+
+GOLD4 = os.path.join(os.path.dirname(__file__), "golden", "n60_seed2_order4.npz")
+GOLD4S = os.path.join(os.path.dirname(__file__), "golden", "n120_seed0_order4_slabs.npz")
+
+
+@pytest.mark.skipif(not os.path.exists(GOLD4), reason="golden file not generated")
+def test_n60_order4_against_stored_oracle(npf):
+    sysm = S.config_n60(2, orders=(4,))
+    ref = np.load(GOLD4)["psi4"]
+    for prec in ("split_bf16", "fp32"):
+        with make_plan(npf, sysm, 4, prec) as p:
+            assert rel_fro(p.term(4), ref) < TOL[prec]
+
+
+@pytest.mark.skipif(not os.path.exists(GOLD4S), reason="golden file not generated")
+def test_n120_order4_slabs_against_stored_oracle(npf):
+    sysm = S.config_n120(0, orders=(4,))
+    g = np.load(GOLD4S)
+    with make_plan(npf, sysm, 4, "split_bf16") as p:
+        for pre, ref in zip(g["prefixes"], g["slabs"]):
+            assert rel_fro(p.modal_slab(4, [int(x) for x in pre]), ref) < 1e-10
