@@ -28,11 +28,13 @@ sys.path.insert(0, ROOT)
 
 N_STATES = 120
 ORDERS = (3, 4)
+# name -> (n, orders)
+WORKLOADS = {"n120": (120, (3, 4)), "n60": (60, (3, 4)), "n120o3": (120, (3,))}
 METRIC = "modal-tensor entries/s & % roofline, split-prec vs native FP64 at rel err <=1e-10"
 
 
-def entries_per_step(n=N_STATES, orders=ORDERS):
-    return sum(n ** (N + 1) for N in orders)
+def entries_per_step(n, orders=None):
+    return sum(n ** (N + 1) for N in (ORDERS if orders is None else orders))
 
 
 def measured_peaks():
@@ -156,6 +158,9 @@ def main():
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="n120", choices=list(WORKLOADS),
+                    help="n120: the measured configuration; the others are small cases for "
+                         "profiler captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -173,7 +178,9 @@ def main():
     from paper_2509_08968_gb300 import build
     build.build()
 
-    sysm = S.config_n120(rank, orders=ORDERS)
+    global N_STATES, ORDERS
+    N_STATES, ORDERS = WORKLOADS[args.workload]
+    sysm = S.config_blocks(N_STATES, rank, orders=ORDERS)
     n = sysm.n
     stream = torch.cuda.current_stream()
     plan = npf.Plan(sysm.lam, sysm.U, sysm.V, max(ORDERS), precision=args.precision,
@@ -275,8 +282,9 @@ def main():
             "dtype": {"split_bf16": "bf16x5-split (fp64-emulating)", "fp32": "bf16x3-split",
                       "fp64": "f64"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": "n=120 block-structured system (30 blocks x 4 states), "
-                                   "NPF orders 3 and 4, packed symmetric A3/A4 30% N(0,1)",
+            "config": {"workload": f"n={n} block-structured system ({n // 4} blocks x 4 states), "
+                                   f"NPF orders {', '.join(map(str, ORDERS))}, packed symmetric "
+                                   "tensors 30% N(0,1)",
                        "n": n, "orders": list(ORDERS), "precision": args.precision,
                        "entries_per_step": entries_per_step(n),
                        "l2": "inputs larger than L2 (packed order-4 tensor 8.7 GB)"},

@@ -7,25 +7,32 @@
 // exact FP32 sum (|d d'| <= 2^14, 2^14 * 256 = 2^22), so the slice pairs (s, t) with s + t < S
 // are accumulated in TMEM by level: L0 = pair (0,0), L1 = pairs (0,1),(1,0) and L2 = the three
 // level-2 pairs are exact FP32 sums (|L2| * 2^16 <= 3 * 2^22 < 2^24); L3 = every deeper level
-// (relative weight <= 2^-24, so even a truncating FP32 accumulation there costs < 2^-40). The
+// (relative weight <= 2^-24, so even a truncating FP32 accumulation there costs ~2^-40). The
 // epilogue recombines V = (L0 + L1 + L2) * 2^30 + rint(L3 * 2^30) exactly in 64-bit integers
-// (|V| <= 2^52, resolution 2^-30 of the L0 unit); the value is V * 2^(e_a + e_b - VEXP) with
-// VEXP = 14 + 30. It then either re-slices V for the next contraction (pure integer
-// arithmetic, new exponent shared by the next operand's K-row) or, for the upper-index
-// contraction, divides by the resonance denominator in native FP64 before re-slicing.
+// (|V| <= 2^53, resolution 2^-30 of the L0 unit); the value is V * 2^(e_a + e_b - VEXP),
+// VEXP = 14 + 30. It then re-slices V for the next contraction (integer arithmetic, new exponent
+// shared by the next operand's K-row), or divides by the resonance denominator in native FP64.
 //
-// Complex data: an operand row stores [Re x (128) | Im x (128)] along K' = 256; the fixed matrix
-// W (Phi or Psi) is stored as 2 x 128 "rows" Re-row p = [Re W[:,p] | -Im W[:,p]] and
-// Im-row p = [Im W[:,p] | Re W[:,p]], so one real GEMM gives Re and Im of X.W.
+// Complex operands interleave (Re, Im) along K': row = [Re x_0, Im x_0, Re x_1, Im x_1, ...]
+// (K' = 256 for 128 complex entries). A fixed complex matrix W is stored as Re-row p =
+// [Re W_0p, -Im W_0p, Re W_1p, -Im W_1p, ..] and Im-row p = [Im W_0p, Re W_0p, ..], so one real
+// GEMM yields Re and Im of X.W; a real operand row has K' = 128 plain entries.
 //
-// Dataflow of one order N (indices padded to NP = 128, batch of `cur` values of the first
-// output index pb = p_N - b0), Algorithm 2 steps 1-19:
-//   first  : rows (j, a_1..a_{N-1}) of the expanded real tensor, K = a_N, new index pb
-//            -> T_1[pb][j][a_1..a_{N-1}]
-//   modes  : rows (pb, rest), K = innermost a, new index p -> [pb][p][rest]  (N-1 times)
-//   divide : rows (pb, p_1..p_{N-1}), K = j, new index i, h = C/(N! D) -> [pb][i][p_1..p_{N-1}]
-//   reduce : G^T[k][c] = sum_{p_{N-1}} psi_{p_{N-1} k} h[c][p_{N-1}], c = (pb, i, p_1..p_{N-2}),
-//            weighted by psi_{p_{N-2} k}, psi_{b0+pb, k}, prod psi_{p_m k} and summed into Psi_N.
+// Dataflow of one order N (Algorithm 2), indices padded to NP = 128:
+//   P1     : S[i][Q] = sum_j psi_{ij} A^j_Q on the packed (sorted) lower tuples Q (real rows Q,
+//            K = j), then per-i digit records of S (the upper index first: step 4 moved ahead,
+//            which the contraction order allows).
+//   batches of `ib` upper indices i (the output index space of Algorithm 1's sizing rule):
+//   expand : rows (i, a_1..a_{N-1}), K = a_N, digits of S^i_{sort(a)}
+//   c = 1..N-1 : contract the innermost a with Phi, new index p in front of the other p's:
+//            [i][p_{N-c+1}][p_{N-c+2}..p_N][a_1..a_{N-c}]
+//   c = N  : last a with Phi, 1/N!, resonance denominator (clamped), multiplicity -> h
+//            [i][p_1][p_2..p_N]
+//   reduce : G^T[k][c'] = sum_{p_N} psi_{p_N k} h[c'][p_N], c' = (i, p_1..p_{N-1}), folded with
+//            psi_{p_{N-1} k} and prod_{m<=N-2} psi_{p_m k} into Psi_N[i][k].
+// h is symmetric in its lower indices, so only non-decreasing tuples p_1 <= .. <= p_N are formed
+// (tiles whose shared p's are unsorted are skipped; elements out of order are masked) and each
+// is weighted by its multiplicity N! / prod(run lengths)! in the reduction.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -43,11 +50,13 @@ namespace npf {
 
 constexpr int NP = 128;        // padded index extent (n <= 128 on this path)
 constexpr int BK = 32;         // K' elements per pipeline chunk (64 bytes, SWIZZLE_64B)
-constexpr int KP = 256;        // K' of a complex operand row
+constexpr int KP = 256;        // K' of a complex operand row (interleaved Re/Im)
 constexpr int EXP_NONE = -4096;
 constexpr int TMEM_COLS = 512;
 constexpr int kErrTimeout = 1;
-constexpr int VEXP = 44;        // value = V * 2^(e_a + e_b - VEXP), V in units of 2^-30 of L0
+constexpr int VEXP = 44;       // value = V * 2^(e_a + e_b - VEXP), V in units of 2^-30 of L0
+constexpr int EPI_WARPS = 8;   // epilogue warps (two per TMEM lane quarter)
+constexpr int ROW_THREADS = 64 + 32 * EPI_WARPS;
 
 // ---------------------------------------------------------------------------------------
 // Integer / double-float helpers
@@ -61,33 +70,35 @@ __device__ __forceinline__ int bitlen64(long long v)
 // W = round(V * 2^sh) for |result| < 2^47.
 __device__ __forceinline__ long long shift_round(long long V, int sh)
 {
-    if (sh >= 0) return V << sh;
+    if (sh >= 0) return sh < 16 ? V << sh : 0;
     const int r = -sh;
     if (r >= 63) return 0;
     return (V + (1ll << (r - 1))) >> r;
 }
 
-// Balanced base-256 digits of W (S digits, most significant first), written as plane values.
+// 2^e for |e| < 1000 (double) / |e| < 127 (float)
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// BF16 bits of d * 2^(-8 s) for an integer digit |d| <= 128 (exact).
+__device__ __forceinline__ uint32_t digit_bf16(int d, int s)
+{
+    return __float_as_uint((float)d * pow2f(-8 * s)) >> 16;
+}
+
+// Balanced base-256 digits of W, packed as (Re, Im) BF16 pairs per plane.
 template <int S>
-__device__ __forceinline__ void digits(long long W, float (&d)[S])
+__device__ __forceinline__ void digit_pairs(long long Wr, long long Wi, uint32_t (&out)[S])
 {
 #pragma unroll
     for (int s = S - 1; s >= 1; --s) {
-        const int lo = (int)((W + 128) & 255) - 128;
-        d[s] = (float)lo;
-        W = (W - lo) >> 8;
+        const int lr = (int)((Wr + 128) & 255) - 128;
+        const int li = (int)((Wi + 128) & 255) - 128;
+        out[s] = digit_bf16(lr, s) | (digit_bf16(li, s) << 16);
+        Wr = (Wr - lr) >> 8;
+        Wi = (Wi - li) >> 8;
     }
-    d[0] = (float)W;
-}
-
-// 2^e as a double for |e| < 1000.
-__device__ __forceinline__ double pow2d(int e)
-{
-    return __longlong_as_double((long long)(1023 + e) << 52);
-}
-__device__ __forceinline__ float pow2f(int e)
-{
-    return __int_as_float((127 + e) << 23);
+    out[0] = digit_bf16((int)Wr, 0) | (digit_bf16((int)Wi, 0) << 16);
 }
 
 struct dfl { float hi, lo; };
@@ -110,7 +121,7 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b)
     return df_norm(p, e);
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
-// exact-to-2^-48 conversion of V * 2^sc
+// V * 2^sc as a double-float (relative error ~2^-48)
 __device__ __forceinline__ dfl df_from_i64(long long V, int sc)
 {
     const float hi = __ll2float_rn(V);
@@ -148,119 +159,94 @@ __device__ __forceinline__ void load_levels(uint32_t taddr, int stride, uint32_t
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Packed-tensor slicing (once per tensor): per upper index j the exponent of max|A^j| and the
-// S digits of every packed entry, stored as 8 int16 (16 bytes) per entry.
-// ---------------------------------------------------------------------------------------
-__global__ void k_row_exp(const double* __restrict__ A, int64_t P, int n, int* __restrict__ E)
+__host__ __device__ constexpr int64_t ipow_np(int e) { return e <= 0 ? 1 : NP * ipow_np(e - 1); }
+
+// digits of r (N-1 digits base NP, most significant first) into d[0..N-2]
+__device__ __forceinline__ void row_digits(int64_t r, int nd, int* d)
 {
-    const int j = blockIdx.x;
+    for (int m = nd - 1; m >= 0; --m) {
+        d[m] = (int)(r % NP);
+        r /= NP;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Input preparation (once per tensor): A^T digit planes for the upper-index contraction,
+// rows = packed lower tuples Q (exponent per Q over all j), K' = j (real).
+// ---------------------------------------------------------------------------------------
+template <int S>
+__global__ void k_prep_at(const double* __restrict__ A, int64_t P, int n,
+                          __nv_bfloat16* __restrict__ planes, int64_t plane_stride,
+                          int* __restrict__ expQ)
+{
+    // one warp per Q row: lanes cover j = lane, lane+32, lane+64, lane+96
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (q >= P) return;
+    double v[4];
     double m = 0.0;
-    for (int64_t q = threadIdx.x; q < P; q += blockDim.x) m = fmax(m, fabs(A[(int64_t)j * P + q]));
-    __shared__ double red[256];
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        int e = EXP_NONE;
-        if (red[0] > 0.0) frexp(red[0], &e);
-        E[j] = e;
-    }
-}
-
-template <int S>
-__global__ void k_slice_packed(const double* __restrict__ A, int64_t P, int n,
-                               const int* __restrict__ E, short* __restrict__ dig)
-{
-    const int64_t tot = (int64_t)n * P;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(idx / P);
-        const int e = E[j];
-        short out[8] = {};
-        if (e != EXP_NONE) {
-            const double x = A[idx] * pow2d(7 + 8 * (S - 1) - e);
-            long long W = __double2ll_rn(x);
 #pragma unroll
-            for (int s = S - 1; s >= 1; --s) {
-                const int lo = (int)((W + 128) & 255) - 128;
-                out[s] = (short)lo;
-                W = (W - lo) >> 8;
+    for (int t = 0; t < 4; ++t) {
+        const int j = lane + 32 * t;
+        v[t] = j < n ? A[(int64_t)j * P + q] : 0.0;
+        m = fmax(m, fabs(v[t]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = EXP_NONE;
+    if (m > 0.0) frexp(m, &e);
+    if (lane == 0) expQ[q] = e;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int j = lane + 32 * t;
+        long long W = 0;
+        if (e != EXP_NONE) W = __double2ll_rn(v[t] * pow2d(7 + 8 * (S - 1) - e));
+#pragma unroll
+        for (int s = S - 1; s >= 0; --s) {
+            int d;
+            if (s > 0) {
+                d = (int)((W + 128) & 255) - 128;
+                W = (W - d) >> 8;
+            } else {
+                d = (int)W;
             }
-            out[0] = (short)W;
+            reinterpret_cast<uint16_t*>(planes)[s * plane_stride + q * NP + j] =
+                (uint16_t)digit_bf16(d, s);
         }
-        uint4 v;
-        memcpy(&v, out, 16);
-        reinterpret_cast<uint4*>(dig)[idx] = v;
-    }
-}
-
-// Dense expansion of the first operand for upper indices j in [j0, j0 + jc):
-// plane_s[(j - j0, a_1..a_{N-1}) * NP + a_N] = digit_s(A^j_{sort(a)}) * 2^(-8 s), zero on padding.
-template <int S>
-__global__ void k_expand_first(const short* __restrict__ dig, int64_t P, int n, int N, int j0,
-                               int jc, const int64_t* __restrict__ cnt,
-                               __nv_bfloat16* __restrict__ planes, int64_t plane_stride)
-{
-    int64_t per_j = 1;
-    for (int m = 0; m < N; ++m) per_j *= NP;
-    const int64_t tot = per_j * jc;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int j = j0 + (int)(idx / per_j);
-        int64_t f = idx % per_j;
-        int a[8];
-        bool pad = j >= n;
-        for (int m = N - 1; m >= 0; --m) {
-            a[m] = (int)(f % NP);
-            f /= NP;
-            pad |= a[m] >= n;
-        }
-        short d[8] = {};
-        if (!pad) {
-            sort_small(a, N);
-            const int64_t q = tuple_rank(a, N, cnt, n);
-            const uint4 v = reinterpret_cast<const uint4*>(dig)[(int64_t)j * P + q];
-            memcpy(d, &v, 16);
-        }
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-            planes[s * plane_stride + idx] = __float2bfloat16_rn((float)d[s] * pow2f(-8 * s));
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// Row-data GEMM (data rows on the M side, the fixed complex matrix on the N side).
+// Row-data GEMM: data rows on the M side (128 per tile), the fixed complex matrix on the N side
+// (bnc complex columns per tile -> 2*bnc real columns: Re block then Im block).
 // ---------------------------------------------------------------------------------------
-enum { EPI_SLICE = 0, EPI_DIVIDE = 1, EPI_F64 = 2 };
+enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3 };
 
 struct RowArgs {
     int a_rows;          // rows per plane in the A tensor map
-    int kch;             // K' chunks of 32 (4: real operand, 8: complex operand)
-    const int* ea;       // row exponents, indexed by (o_base + local row) >> ea_shift
+    int kch;             // K' chunks of 32
+    const int* ea;       // row exponents, indexed by (local row) >> ea_shift
     int ea_shift;
-    int64_t ea_off;      // subtracted from the shifted index
     const int* eb;       // column exponents of the fixed matrix (256 entries)
-    int bcol0;           // first fixed-matrix column of column tile 0
-    int bnc;             // complex columns per tile (multiple of 8, <= 64)
+    int bnc;             // complex columns per tile (64)
     int ncol_tiles;
-    int ncols_valid;     // output columns q = tile*bnc + c valid below this
     int64_t num_tiles;
-    int64_t o_base;      // global row index of local row 0
-    int64_t R;           // output layout [outer][q][r], o = outer*R + r
-    int npc;             // extent of q in the output layout
+    int N;               // order
+    int c;               // contraction index 1..N (0: upper-index contraction P1)
+    int64_t R;           // rows per outer index (output layout [outer][q][r])
+    int npc;             // extent of the new index in the output layout
+    int n;
     __nv_bfloat16* out_planes;
     int64_t out_plane_stride;
     int* out_exp;
-    double2* out_f64;    // EPI_F64: out[o * 128 + q] for the global row o
-    // EPI_DIVIDE
+    double2* out_f64;    // EPI_F64T: out[q * ld_f64 + o]; EPI_SLAB: out[i * n + q]
+    int64_t ld_f64;
+    // EPI_DIVIDE / EPI_SLAB
     const double2* lam;
-    int n, N, b0;
+    int i0;
     double invfact, eps;
     int divide;
+    int pre[8];          // EPI_SLAB: the requested sorted prefix (N-1 indices)
     int* err;
 };
 
@@ -270,13 +256,32 @@ struct RowCfg {
     static constexpr int A_TILE = NP * BK * 2;                 // 8 KB
     static constexpr int B_TILE = NP * BK * 2;                 // up to 128 rows: 8 KB
     static constexpr int STAGE_BYTES = S * (A_TILE + B_TILE);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 1024;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 2048;
+    static_assert(STAGES * STAGE_BYTES >= 128 * 64 * 16, "epilogue staging must fit");
 };
 
+// Is the non-decreasing order of the row's p indices (and the new column) broken?
+// For contraction c the row r = (p_{N-c+2}..p_N, a_1..a_{N-c}) carries c-1 p's.
+__device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_local, int ct)
+{
+    if (a.c < 2) return false;
+    const int64_t r = row0_local % a.R;
+    int d[8];
+    row_digits(r, a.N - 1, d);
+    const int np = a.c - 1;                       // p's in the row
+    const int shared = (a.c < a.N) ? np : np - 1; // p's constant over the tile
+    for (int m = 1; m < shared; ++m)
+        if (d[m - 1] > d[m]) return true;
+    for (int m = 0; m < shared; ++m)
+        if (d[m] >= a.n) return true;                     // padding index: all zero
+    if (shared >= 1 && ct * a.bnc > d[0]) return true;   // every new index > first p
+    return false;
+}
+
 template <int S, int MODE>
-__global__ void __launch_bounds__(192, 1)
-    k_ozaki_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 RowArgs args)
+__global__ void __launch_bounds__(ROW_THREADS, 1)
+    k_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           RowArgs args)
 {
     using C = RowCfg<S>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -292,8 +297,9 @@ __global__ void __launch_bounds__(192, 1)
     const int64_t tile = blockIdx.x;
     const int ct = (int)(tile % args.ncol_tiles);
     const int64_t rt = tile / args.ncol_tiles;
-    const int64_t row0 = rt * NP;                // local row of this tile
-    const int bnr = 2 * args.bnc;                // B rows (Re + Im) per tile
+    const int64_t row0 = rt * NP;
+    if (tile_skipped(args, row0, ct)) return;   // uniform over the CTA
+    const int bnr = 2 * args.bnc;
     const uint32_t b_bytes_tile = (uint32_t)bnr * BK * 2;
 
     if (threadIdx.x == 0) {
@@ -318,6 +324,7 @@ __global__ void __launch_bounds__(192, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
+        const int bc = ct * args.bnc;
         for (int kc = 0; kc < args.kch; ++kc) {
             const int st = kc % C::STAGES;
             const uint32_t ph = (kc / C::STAGES) & 1;
@@ -328,7 +335,6 @@ __global__ void __launch_bounds__(192, 1)
             for (int s = 0; s < S; ++s)
                 tc::tma_load_2d(sA + s * C::A_TILE, &tmA, kc * BK, s * args.a_rows + (int)row0,
                                 &full[st]);
-            const int bc = args.bcol0 + ct * args.bnc;
             for (int t = 0; t < S; ++t) {
                 uint8_t* dst = sB + t * C::B_TILE;
                 tc::tma_load_2d(dst, &tmB, kc * BK, t * 512 + bc, &full[st]);
@@ -337,14 +343,13 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer: slice pairs (s, t), s + t < S, accumulated by level
         const uint32_t idesc = tc::idesc_bf16_f32(128, bnr);
         bool first[4] = {true, true, true, true};
-        bool ok = true;
-        for (int kc = 0; kc < args.kch && ok; ++kc) {
+        for (int kc = 0; kc < args.kch; ++kc) {
             const int st = kc % C::STAGES;
             const uint32_t ph = (kc / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) { ok = false; break; }
+            if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) break;
             tc::fence_after_sync();
             const uint32_t aBase = tc::smem_u32(stage_base + st * C::STAGE_BYTES);
             const uint32_t bBase = aBase + S * C::A_TILE;
@@ -365,123 +370,168 @@ __global__ void __launch_bounds__(192, 1)
         }
         tc::mma_commit(acc_full);
     } else if (warp >= 2) {
-        // ---------------- epilogue (4 warps, TMEM lane quarter = warp % 4)
+        // ---------------- epilogue: 8 warps, lane quarter = warp % 4, column half = (warp-2)/4
         const int q4 = warp % 4;
+        const int half = (warp - 2) / 4;
         const int rl = q4 * 32 + lane;                      // local row within the tile
-        const int64_t o = args.o_base + row0 + rl;          // global row
+        const int64_t o = row0 + rl;                        // local row of the launch
         const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
         const bool ok = tc::mbar_wait(acc_full, 0, args.err, kErrTimeout);
         tc::fence_after_sync();
-        const int ea = args.ea[((o) >> args.ea_shift) - args.ea_off];
         const int bnc = args.bnc;
+        const int cols = bnc / 2;
+        const int cbeg = half * cols;
         const int qbase = ct * bnc;
-        // output addressing (rotation)
+        const int ea = args.ea[o >> args.ea_shift];
         const int64_t outer = o / args.R;
-        const int64_t rr = o % args.R;                      // rr % 128 == rl
+        const int64_t rr = o % args.R;
         const int64_t rblk = rr / NP;
         const int64_t rperq = args.R / NP;
+        const int N = args.N, n = args.n;
 
-        // EPI_DIVIDE: row denominators
+        // row p's (c >= 1): digits of rr, the first c-1 are p's
+        int dg[8];
+        row_digits(rr, N - 1, dg);
+        const int np_row = args.c >= 1 ? args.c - 1 : 0;
+        bool row_ok = true;
+        for (int m = 1; m < np_row; ++m) row_ok &= dg[m - 1] <= dg[m];
+        for (int m = 0; m < np_row; ++m) row_ok &= dg[m] < n;
+        const int firstp = np_row >= 1 ? dg[0] : NP;
+
+        // EPI_DIVIDE / EPI_SLAB: sigma of the row p's, multiplicity base and first run length
         double2 sigma = make_double2(0, 0);
-        bool rowpad = false;
-        if (MODE != EPI_SLICE) {
-            int64_t f = rr;
-            for (int m = 0; m < args.N - 1; ++m) {
-                const int pm = (int)(f % NP);
-                f /= NP;
-                if (pm >= args.n) rowpad = true;
-                else sigma = cadd(sigma, args.lam[pm]);
+        double mult_base = 1.0;
+        int run1 = 1;
+        if (MODE == EPI_DIVIDE || MODE == EPI_SLAB) {
+            if (row_ok) {
+                for (int m = 0; m < np_row; ++m) sigma = cadd(sigma, args.lam[dg[m]]);
+                sigma = csub(sigma, args.lam[args.i0 + (int)outer]);
             }
-            sigma = cadd(sigma, args.lam[args.b0 + (int)outer]);
+            double denom = 1.0;
+            int run = 1;
+            for (int m = 1; m <= np_row; ++m) {
+                if (m < np_row && dg[m] == dg[m - 1]) {
+                    ++run;
+                } else {
+                    if (m - run == 0) run1 = run;
+                    for (int t = 2; t <= run; ++t) denom *= t;
+                    run = 1;
+                }
+            }
+            double nf = 1.0;
+            for (int t = 2; t <= N; ++t) nf *= t;
+            mult_base = nf / denom;
         }
-        double2* hbuf = (double2*)stage_base;             // [128][64] FP64 (pipeline drained)
+        long long* vbuf = (long long*)stage_base;     // [64 cols][128 rows][2] (pipeline drained)
+        double2* hbuf = (double2*)stage_base;         // same storage, FP64 quotients
 
         if (ok) {
-            // pass 1: exponents (and FP64 quotients for the divide)
-            for (int c8 = 0; c8 < bnc; c8 += 8) {
+            // pass 1: recombine, exponents (and FP64 quotients), stage in shared memory
+            for (int c8 = cbeg; c8 < cbeg + cols; c8 += 8) {
                 uint32_t rv[4][8], iv[4][8];
                 load_levels<S>(trow + c8, 128, rv);
                 load_levels<S>(trow + bnc + c8, 128, iv);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const int qc = qbase + c8 + c;
-                    const int eb = args.eb[args.bcol0 + qc];
+                    const int cl = c8 + c;
+                    const int qc = qbase + cl;
+                    const int eb = args.eb[qc];
                     const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                     const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
+                    const bool valid = row_ok && qc < n && (args.c < 2 || qc <= firstp);
                     unsigned key = 0;
-                    if (MODE == EPI_SLICE) {
+                    if (MODE == EPI_SLICE || MODE == EPI_F64T) {
+                        vbuf[((size_t)cl * NP + rl) * 2 + 0] = Vr;
+                        vbuf[((size_t)cl * NP + rl) * 2 + 1] = Vi;
                         const int bl = max(bitlen64(Vr), bitlen64(Vi));
-                        if (bl) key = (unsigned)(bl + ea + eb - VEXP + 8192);
+                        if (valid && bl) key = (unsigned)(bl + ea + eb - VEXP + 8192);
                     } else {
                         double2 h = make_double2(0, 0);
-                        if (!rowpad && qc < args.n && (Vr | Vi)) {
-                            const double sc = pow2d(ea + eb - VEXP) * args.invfact;
+                        if (valid && (Vr | Vi)) {
+                            const double mult = (qc == firstp) ? mult_base / (run1 + 1) : mult_base;
+                            const double sc = pow2d(ea + eb - VEXP) * args.invfact *
+                                              (MODE == EPI_DIVIDE ? mult : 1.0);
                             h = make_double2((double)Vr * sc, (double)Vi * sc);
                             if (args.divide) {
-                                const double2 D =
-                                    clamp_denominator(csub(sigma, args.lam[qc]), args.eps);
+                                const double2 D = clamp_denominator(cadd(sigma, args.lam[qc]), args.eps);
                                 h = cdiv_smith(h, D);
                             }
                         }
-                        hbuf[rl * 64 + c8 + c] = h;
-                        const double m = fmax(fabs(h.x), fabs(h.y));
-                        if (m > 0.0) {
+                        hbuf[(size_t)cl * NP + rl] = h;
+                        const double mm = fmax(fabs(h.x), fabs(h.y));
+                        if (mm > 0.0) {
                             int e;
-                            frexp(m, &e);
+                            frexp(mm, &e);
                             key = (unsigned)(e + 8192);
                         }
                     }
                     const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
-                    if (lane == 0 && wmax) atomicMax(&colE[c8 + c], (int)wmax);
+                    if (lane == 0 && wmax) atomicMax(&colE[cl], (int)wmax);
                 }
             }
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
         if (ok) {
-            // pass 2: digits of the next operand (or FP64 store)
-            for (int c8 = 0; c8 < bnc; c8 += 8) {
-                uint32_t rv[4][8], iv[4][8];
-                if (MODE == EPI_SLICE) {
-                    load_levels<S>(trow + c8, 128, rv);
-                    load_levels<S>(trow + bnc + c8, 128, iv);
-                    tc::tmem_wait_ld();
+            // pass 2: outputs
+            for (int cl = cbeg; cl < cbeg + cols; ++cl) {
+                const int qc = qbase + cl;
+                if (qc >= args.npc) continue;
+                const int key = colE[cl];
+                if (MODE == EPI_F64T) {
+                    if (qc < n) {
+                        const long long Vr = vbuf[((size_t)cl * NP + rl) * 2 + 0];
+                        const long long Vi = vbuf[((size_t)cl * NP + rl) * 2 + 1];
+                        const double sc = pow2d(ea + args.eb[qc] - VEXP);
+                        args.out_f64[(int64_t)qc * args.ld_f64 + o] =
+                            make_double2((double)Vr * sc, (double)Vi * sc);
+                    }
+                    continue;
                 }
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int qc = qbase + c8 + c;
-                    if (qc >= args.ncols_valid) continue;
-                    const int key = colE[c8 + c];
-                    const int E = key ? key - 8192 : EXP_NONE;
-                    if (MODE == EPI_F64) {
-                        args.out_f64[o * NP + qc] = hbuf[rl * 64 + c8 + c];
-                        continue;
+                if (MODE == EPI_SLAB) {
+                    // store h^i_{pre, q} when sort(pre + q) equals this element's tuple
+                    const double2 h = hbuf[(size_t)cl * NP + rl];
+                    int t[8];
+                    t[0] = qc;
+                    for (int m = 0; m < np_row; ++m) t[m + 1] = dg[m];
+                    // multiset difference t \ pre must be a single index
+                    int used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    int matched = 0, extra = -1, nextra = 0;
+                    for (int a = 0; a < N; ++a) {
+                        bool hit = false;
+                        for (int b = 0; b < N - 1 && !hit; ++b)
+                            if (!used[b] && args.pre[b] == t[a]) { used[b] = 1; hit = true; }
+                        if (hit) ++matched;
+                        else { extra = t[a]; ++nextra; }
                     }
-                    const int64_t rowp = (outer * args.npc + qc) * rperq + rblk;
-                    float dr[S], di[S];
-                    if (key == 0) {
-#pragma unroll
-                        for (int s = 0; s < S; ++s) dr[s] = di[s] = 0.f;
-                    } else if (MODE == EPI_SLICE) {
-                        const int eb = args.eb[args.bcol0 + qc];
-                        const int sh = ea + eb - VEXP - E + 7 + 8 * (S - 1);
-                        digits<S>(shift_round(combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]), sh), dr);
-                        digits<S>(shift_round(combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]), sh), di);
-                    } else {
-                        const double2 h = hbuf[rl * 64 + c8 + c];
-                        const double sc = pow2d(7 + 8 * (S - 1) - E);
-                        digits<S>(__double2ll_rn(h.x * sc), dr);
-                        digits<S>(__double2ll_rn(h.y * sc), di);
-                    }
-                    __nv_bfloat16* dst = args.out_planes + rowp * KP + rl;
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        dst[s * args.out_plane_stride] = __float2bfloat16_rn(dr[s] * pow2f(-8 * s));
-                        dst[s * args.out_plane_stride + NP] =
-                            __float2bfloat16_rn(di[s] * pow2f(-8 * s));
-                    }
-                    if (rl == 0) args.out_exp[rowp] = E;
+                    const bool valid = row_ok && qc < n && (args.c < 2 || qc <= firstp);
+                    if (valid && matched == N - 1 && nextra == 1)
+                        args.out_f64[(int64_t)(args.i0 + outer) * n + extra] = h;
+                    continue;
                 }
+                if (args.c >= 2 && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
+                const int64_t rowp = (outer * args.npc + qc) * rperq + rblk;
+                const int E = key ? key - 8192 : EXP_NONE;
+                uint32_t w[S];
+                if (key == 0) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) w[s] = 0u;
+                } else if (MODE == EPI_SLICE) {
+                    const int sh = ea + args.eb[qc] - VEXP - E + 7 + 8 * (S - 1);
+                    const long long Vr = vbuf[((size_t)cl * NP + rl) * 2 + 0];
+                    const long long Vi = vbuf[((size_t)cl * NP + rl) * 2 + 1];
+                    const bool valid = row_ok && qc < n;
+                    digit_pairs<S>(valid ? shift_round(Vr, sh) : 0, valid ? shift_round(Vi, sh) : 0,
+                                   w);
+                } else {
+                    const double2 h = hbuf[(size_t)cl * NP + rl];
+                    const double sc = pow2d(7 + 8 * (S - 1) - E);
+                    digit_pairs<S>(__double2ll_rn(h.x * sc), __double2ll_rn(h.y * sc), w);
+                }
+                uint32_t* dst = reinterpret_cast<uint32_t*>(args.out_planes) + rowp * (KP / 2) + rl;
+#pragma unroll
+                for (int s = 0; s < S; ++s) dst[s * (args.out_plane_stride / 2)] = w[s];
+                if (rl == 0) args.out_exp[rowp] = E;
             }
         }
     }
@@ -494,20 +544,104 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 // ---------------------------------------------------------------------------------------
-// Reduction GEMM: G^T[k][c] = sum_p psi_{p k} h[c][p] with the fixed Psi^T on the M side (Re
-// rows and Im rows as two MMA streams) and the h rows c on the N side; each thread (one k)
-// folds its columns with the Khatri-Rao weights in double-float and adds -sum into Psi_N[i][k].
+// Digit records of S^i_Q (per upper index i, exponent over all Q) for the dense expansion.
+// ---------------------------------------------------------------------------------------
+__global__ void k_s_exp(const double2* __restrict__ Sd, int64_t ld, int64_t P, int* __restrict__ E)
+{
+    const int i = blockIdx.x;
+    double m = 0.0;
+    for (int64_t q = threadIdx.x; q < P; q += blockDim.x) {
+        const double2 v = Sd[(int64_t)i * ld + q];
+        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int e = EXP_NONE;
+        if (red[0] > 0.0) frexp(red[0], &e);
+        E[i] = e;
+    }
+}
+
+// rec[i*P + q] = 8 x uint32: (Re, Im) BF16 digit pairs of S^i_q for planes 0..S-1
+template <int S>
+__global__ void k_s_records(const double2* __restrict__ Sd, int64_t ld, int64_t P, int n,
+                            const int* __restrict__ E, uint4* __restrict__ rec)
+{
+    const int64_t tot = (int64_t)n * P;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / P);
+        const int64_t q = idx % P;
+        const int e = E[i];
+        uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (e != EXP_NONE) {
+            const double2 v = Sd[(int64_t)i * ld + q];
+            const double sc = pow2d(7 + 8 * (S - 1) - e);
+            uint32_t ww[S];
+            digit_pairs<S>(__double2ll_rn(v.x * sc), __double2ll_rn(v.y * sc), ww);
+#pragma unroll
+            for (int s = 0; s < S; ++s) w[s] = ww[s];
+        }
+        rec[idx * 2 + 0] = make_uint4(w[0], w[1], w[2], w[3]);
+        rec[idx * 2 + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+// Dense expansion for upper indices i in [i0, i0 + ib): row (i - i0, a_1..a_{N-1}), K pos a_N.
+template <int S>
+__global__ void k_expand(const uint4* __restrict__ rec, int64_t P, int n, int N, int i0, int ib,
+                         const int64_t* __restrict__ cnt, uint32_t* __restrict__ planes,
+                         int64_t plane_stride_u32)
+{
+    int64_t per_i = 1;
+    for (int m = 0; m < N; ++m) per_i *= NP;
+    const int64_t tot = per_i * ib;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = i0 + (int)(idx / per_i);
+        int64_t f = idx % per_i;
+        int a[8];
+        bool pad = false;
+        for (int m = N - 1; m >= 0; --m) {
+            a[m] = (int)(f % NP);
+            f /= NP;
+            pad |= a[m] >= n;
+        }
+        uint4 r0 = make_uint4(0, 0, 0, 0), r1 = make_uint4(0, 0, 0, 0);
+        if (!pad) {
+            sort_small(a, N);
+            const int64_t q = tuple_rank(a, N, cnt, n);
+            r0 = rec[((int64_t)i * P + q) * 2 + 0];
+            r1 = rec[((int64_t)i * P + q) * 2 + 1];
+        }
+        const uint32_t w[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+        for (int s = 0; s < S; ++s) planes[s * plane_stride_u32 + idx] = w[s];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Reduction GEMM: G^T[k][c'] = sum_{p_N} psi_{p_N k} h[c'][p_N] with Psi^T on the M side (Re
+// rows and Im rows as two MMA streams) and the h rows c' = (i, p_1..p_{N-1}) on the N side;
+// each thread (one k) folds its columns with psi_{p_{N-1} k} in double-float, multiplies by
+// prod_{m<=N-2} psi_{p_m k} and adds -sum into Psi_N[i][k].
 // ---------------------------------------------------------------------------------------
 struct RedArgs {
     int kch;
     const int* ea;        // [128] exponents of Psi^T rows k
     int b_rows;           // rows per plane in the h tensor map
-    const int* eb;        // exponents of h rows c
-    int bnc;              // columns per tile (64)
+    const int* eb;        // exponents of h rows c'
+    int bnc;              // columns per tile
     int64_t num_tiles;
     const float4* psi_df; // psi_{p k} as double-float (re.hi, re.lo, im.hi, im.lo) at p*n + k
     const double2* V;     // psi_{p k} at p*n + k
-    int n, N, b0;
+    int n, N, i0;
     double2* psiN;        // [n][n], accumulated with atomics (subtracting)
     int* err;
 };
@@ -524,8 +658,8 @@ struct RedCfg {
 
 template <int S>
 __global__ void __launch_bounds__(192, 1)
-    k_ozaki_reduce(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   RedArgs args)
+    k_reduce(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             RedArgs args)
 {
     using C = RedCfg<S>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -537,6 +671,17 @@ __global__ void __launch_bounds__(192, 1)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t c0 = (int64_t)blockIdx.x * args.bnc;   // first h row of this tile
+    const int n = args.n, N = args.N;
+    // c' = (i, p_1..p_{N-1}) base NP below i; the tile shares (i, p_1..p_{N-2})
+    int dp[8];
+    row_digits(c0 % ipow_np(N - 1), N - 1, dp);
+    {
+        bool skip = false;
+        for (int m = 1; m < N - 2 + 0; ++m) skip |= dp[m - 1] > dp[m];
+        for (int m = 0; m < N - 2; ++m) skip |= dp[m] >= n;
+        if (N >= 3 && (int)(c0 % NP) + args.bnc - 1 < dp[N - 3]) skip = true;
+        if (skip) return;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -577,11 +722,10 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = tc::idesc_bf16_f32(128, bnc);
         bool first[4] = {true, true, true, true};
-        bool ok = true;
-        for (int kc = 0; kc < args.kch && ok; ++kc) {
+        for (int kc = 0; kc < args.kch; ++kc) {
             const int st = kc % C::STAGES;
             const uint32_t ph = (kc / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) { ok = false; break; }
+            if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) break;
             tc::fence_after_sync();
             const uint32_t aBase = tc::smem_u32(smem + st * C::STAGE_BYTES);
             const uint32_t bBase = aBase + 2 * S * C::A_TILE;
@@ -611,12 +755,9 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
         const bool ok = tc::mbar_wait(acc_full, 0, args.err, kErrTimeout);
         tc::fence_after_sync();
-        const int n = args.n, N = args.N;
         if (ok) {
             const int ea = k < n ? args.ea[k] : 0;
-            // column c = (pb, i, p_1..p_{N-2}); for N >= 3 the tile shares (pb, i, p_1..p_{N-3})
-            int64_t per_i = 1;
-            for (int m = 0; m < N - 2; ++m) per_i *= NP;
+            const int lowp = N >= 3 ? dp[N - 3] : 0;   // p_{N-2} (columns need p_{N-1} >= it)
             dfl sr = {0.f, 0.f}, si = {0.f, 0.f};
             for (int c8 = 0; c8 < bnc; c8 += 8) {
                 uint32_t rv[4][8], iv[4][8];
@@ -626,49 +767,26 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int64_t col = c0 + c8 + c;
+                    const int p = (int)(col % NP);           // p_{N-1}
+                    if (k >= n || p >= n || p < lowp) continue;
                     const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                     const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                    if (k >= n || !(Vr | Vi)) continue;
+                    if (!(Vr | Vi)) continue;
                     const int sc = ea + args.eb[col] - VEXP;
                     const dfl gr = df_from_i64(Vr, sc), gi = df_from_i64(Vi, sc);
-                    if (N >= 3) {
-                        const int p = (int)(col % NP);
-                        if (p >= n) continue;
-                        const float4 w = args.psi_df[(int64_t)p * n + k];
-                        const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
-                        sr = df_add(sr, df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi))));
-                        si = df_add(si, df_add(df_mul(gr, wi), df_mul(gi, wr)));
-                    } else {
-                        // N == 2: column c = (pb, i); weight psi_{b0+pb, k}
-                        const int i = (int)(col % NP);
-                        const int pb = (int)(col / NP);
-                        if (i >= n) continue;
-                        const double2 w = args.V[(int64_t)(args.b0 + pb) * n + k];
-                        const double2 g = make_double2(df_to_d(gr), df_to_d(gi));
-                        const double2 t = cmul(g, w);
-                        atomicAdd(&args.psiN[(int64_t)i * n + k].x, -t.x);
-                        atomicAdd(&args.psiN[(int64_t)i * n + k].y, -t.y);
-                    }
+                    const float4 w = args.psi_df[(int64_t)p * n + k];
+                    const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
+                    sr = df_add(sr, df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi))));
+                    si = df_add(si, df_add(df_mul(gr, wi), df_mul(gi, wr)));
                 }
             }
-            if (k < n && N >= 3 && (sr.hi != 0.f || si.hi != 0.f)) {
-                int64_t f = c0 / NP;                 // (pb, i, p_1..p_{N-3})
+            if (k < n && (sr.hi != 0.f || si.hi != 0.f)) {
                 double2 w = make_double2(1.0, 0.0);
-                bool pad = false;
-                for (int m = 0; m < N - 3; ++m) {
-                    const int pm = (int)(f % NP);
-                    f /= NP;
-                    if (pm >= n) pad = true;
-                    else w = cmul(w, args.V[(int64_t)pm * n + k]);
-                }
-                const int i = (int)(f % NP);
-                const int pb = (int)(f / NP);
-                if (!pad && i < n) {
-                    w = cmul(w, args.V[(int64_t)(args.b0 + pb) * n + k]);
-                    const double2 t = cmul(make_double2(df_to_d(sr), df_to_d(si)), w);
-                    atomicAdd(&args.psiN[(int64_t)i * n + k].x, -t.x);
-                    atomicAdd(&args.psiN[(int64_t)i * n + k].y, -t.y);
-                }
+                for (int m = 0; m < N - 2; ++m) w = cmul(w, args.V[(int64_t)dp[m] * n + k]);
+                const int i = args.i0 + (int)(c0 / ipow_np(N - 1));
+                const double2 t = cmul(make_double2(df_to_d(sr), df_to_d(si)), w);
+                atomicAdd(&args.psiN[(int64_t)i * n + k].x, -t.x);
+                atomicAdd(&args.psiN[(int64_t)i * n + k].y, -t.y);
             }
         }
     }
@@ -685,15 +803,16 @@ __global__ void __launch_bounds__(192, 1)
 // =======================================================================================
 struct SplitOperand {
     int S = 0;
-    // fixed matrices: planes [S][512 rows][256] bf16 and exponents [256]
-    __nv_bfloat16* phi = nullptr;   int* phi_e = nullptr;    // Phi (columns p)
-    __nv_bfloat16* psi = nullptr;   int* psi_e = nullptr;    // Psi (columns i, K = j)
-    __nv_bfloat16* red = nullptr;   int* red_e = nullptr;    // Psi^T rows k (K = p)
+    // fixed matrices: planes [S][512 rows][K'] bf16 and exponents [256]
+    __nv_bfloat16* phi = nullptr;   int* phi_e = nullptr;    // Phi, complex K (a), columns p
+    __nv_bfloat16* psir = nullptr;  int* psir_e = nullptr;   // Psi, real K (j), columns i
+    __nv_bfloat16* red = nullptr;   int* red_e = nullptr;    // Psi^T rows k, complex K (p)
     float4* psi_df = nullptr;
-    // packed tensor digits per order
-    short* dig[kMaxOrder + 1] = {};
-    int* dexp[kMaxOrder + 1] = {};
-    const double* dig_src[kMaxOrder + 1] = {};
+    // per order: A^T digit planes (rows Q, K' = j) and row exponents
+    __nv_bfloat16* at[kMaxOrder + 1] = {};
+    int* at_e[kMaxOrder + 1] = {};
+    int64_t at_rows[kMaxOrder + 1] = {};
+    const double* at_src[kMaxOrder + 1] = {};
     int* err = nullptr;
 };
 
@@ -724,39 +843,46 @@ static CUtensorMap make_tmap(const void* base, int64_t inner, int64_t rows, int 
                              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                              CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) fail(NPF_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    if (r != CUDA_SUCCESS)
+        fail(NPF_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return m;
 }
 
-static int default_slices(const Plan& p) { return p.slices ? p.slices : (p.precision == NPF_PREC_FP32 ? 3 : 6); }
-
-// Host slicing of a complex value set sharing exponent e (balanced digits, as on the device).
-static void host_digits(double x, int e, int S, float* d)
+static int default_slices(const Plan& p)
 {
-    if (e == EXP_NONE || x == 0.0) { for (int s = 0; s < S; ++s) d[s] = 0.f; return; }
+    return p.slices ? p.slices : (p.precision == NPF_PREC_FP32 ? 3 : 6);
+}
+
+// Host slicing of x with exponent e into S balanced digits.
+static void host_digits(double x, int e, int S, int* d)
+{
+    if (e == EXP_NONE || x == 0.0) { for (int s = 0; s < S; ++s) d[s] = 0; return; }
     long long W = std::llrint(std::ldexp(x, 7 + 8 * (S - 1) - e));
     for (int s = S - 1; s >= 1; --s) {
         const int lo = (int)((W + 128) & 255) - 128;
-        d[s] = (float)lo;
+        d[s] = lo;
         W = (W - lo) >> 8;
     }
-    d[0] = (float)W;
+    d[0] = (int)W;
 }
 
-static uint16_t bf16_bits(float f)
+static uint16_t bf16_of_digit(int d, int s)
 {
-    // exact for the digit values used here (<= 8 significant bits): truncate the low mantissa
+    const float f = std::ldexp((float)d, -8 * s);   // exact: |d| <= 128
     uint32_t u;
     std::memcpy(&u, &f, 4);
     return (uint16_t)(u >> 16);
 }
 
-// Build fixed planes for a complex n x n matrix M accessed as M(kidx, col) (K index first):
-// Re-row col = [Re M(:,col) | -Im M(:,col)], Im-row col = [Im M(:,col) | Re M(:,col)].
+// Fixed planes [S][512][kw] of an n x n complex matrix accessed as get(kidx, col):
+// complex K (kw = 256, interleaved): Re-row col = [Re, -Im, ..], Im-row col = [Im, Re, ..];
+// real K (kw = 128): Re-row col = [Re ..], Im-row col = [Im ..]. Exponent per column.
 template <class F>
-static void build_fixed(int n, int S, F get, std::vector<uint16_t>& planes, std::vector<int>& ex)
+static void build_fixed(int n, int S, bool complexK, F get, std::vector<uint16_t>& planes,
+                        std::vector<int>& ex)
 {
-    planes.assign((size_t)S * 512 * KP, 0);
+    const int kw = complexK ? KP : NP;
+    planes.assign((size_t)S * 512 * kw, 0);
     ex.assign(256, EXP_NONE);
     for (int c = 0; c < n; ++c) {
         double m = 0.0;
@@ -769,16 +895,22 @@ static void build_fixed(int n, int S, F get, std::vector<uint16_t>& planes, std:
         ex[c] = e;
         for (int k = 0; k < n; ++k) {
             const double2 v = get(k, c);
-            float dr[8], di[8];
+            int dr[8], di[8];
             host_digits(v.x, e, S, dr);
             host_digits(v.y, e, S, di);
             for (int s = 0; s < S; ++s) {
-                const float sc = std::ldexp(1.0f, -8 * s);
-                uint16_t* P = planes.data() + (size_t)s * 512 * KP;
-                P[(size_t)c * KP + k] = bf16_bits(dr[s] * sc);            // Re-row: Re part
-                P[(size_t)c * KP + NP + k] = bf16_bits(-di[s] * sc);      //         -Im part
-                P[(size_t)(256 + c) * KP + k] = bf16_bits(di[s] * sc);    // Im-row: Im part
-                P[(size_t)(256 + c) * KP + NP + k] = bf16_bits(dr[s] * sc);
+                uint16_t* P = planes.data() + (size_t)s * 512 * kw;
+                uint16_t* re_row = P + (size_t)c * kw;
+                uint16_t* im_row = P + (size_t)(256 + c) * kw;
+                if (complexK) {
+                    re_row[2 * k] = bf16_of_digit(dr[s], s);
+                    re_row[2 * k + 1] = bf16_of_digit(-di[s], s);
+                    im_row[2 * k] = bf16_of_digit(di[s], s);
+                    im_row[2 * k + 1] = bf16_of_digit(dr[s], s);
+                } else {
+                    re_row[k] = bf16_of_digit(dr[s], s);
+                    im_row[k] = bf16_of_digit(di[s], s);
+                }
             }
         }
     }
@@ -798,10 +930,10 @@ void split_release(Plan& p)
     SplitOperand* so = p.split;
     if (!so) return;
     cudaFree(so->phi); cudaFree(so->phi_e);
-    cudaFree(so->psi); cudaFree(so->psi_e);
+    cudaFree(so->psir); cudaFree(so->psir_e);
     cudaFree(so->red); cudaFree(so->red_e);
     cudaFree(so->psi_df);
-    for (int N = 0; N <= kMaxOrder; ++N) { cudaFree(so->dig[N]); cudaFree(so->dexp[N]); }
+    for (int N = 0; N <= kMaxOrder; ++N) { cudaFree(so->at[N]); cudaFree(so->at_e[N]); }
     cudaFree(so->err);
     delete so;
     p.split = nullptr;
@@ -812,10 +944,11 @@ static void set_smem_attrs()
 {
     static bool done = false;
     if (done) return;
-    NPF_CUDA(cudaFuncSetAttribute(k_ozaki_rows<S, EPI_SLICE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_ozaki_rows<S, EPI_DIVIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_ozaki_rows<S, EPI_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_ozaki_reduce<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RedCfg<S>::SMEM));
+    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_F64T>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
+    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_SLICE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
+    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_DIVIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
+    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_SLAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
+    NPF_CUDA(cudaFuncSetAttribute(k_reduce<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RedCfg<S>::SMEM));
     done = true;
 }
 
@@ -835,15 +968,15 @@ static SplitOperand& prepare(Plan& p)
     std::vector<uint16_t> planes;
     std::vector<int> ex;
     // Phi: K index a, column p: phi_{a p}
-    build_fixed(n, S, [&](int a, int c) { return U[(size_t)a * n + c]; }, planes, ex);
+    build_fixed(n, S, true, [&](int a, int c) { return U[(size_t)a * n + c]; }, planes, ex);
     so->phi = (__nv_bfloat16*)upload(planes);
     so->phi_e = upload(ex);
-    // Psi for the upper-index contraction: K index j, column i: psi_{i j}
-    build_fixed(n, S, [&](int j, int i) { return V[(size_t)i * n + j]; }, planes, ex);
-    so->psi = (__nv_bfloat16*)upload(planes);
-    so->psi_e = upload(ex);
-    // Psi^T rows k for the reduction: K index p, row k: psi_{p k}
-    build_fixed(n, S, [&](int pidx, int k) { return V[(size_t)pidx * n + k]; }, planes, ex);
+    // Psi for the upper-index contraction: real K index j, column i: psi_{i j}
+    build_fixed(n, S, false, [&](int j, int i) { return V[(size_t)i * n + j]; }, planes, ex);
+    so->psir = (__nv_bfloat16*)upload(planes);
+    so->psir_e = upload(ex);
+    // Psi^T rows k for the reduction: complex K index p, row k: psi_{p k}
+    build_fixed(n, S, true, [&](int pidx, int k) { return V[(size_t)pidx * n + k]; }, planes, ex);
     so->red = (__nv_bfloat16*)upload(planes);
     so->red_e = upload(ex);
     std::vector<float4> pdf((size_t)n * n);
@@ -857,86 +990,57 @@ static SplitOperand& prepare(Plan& p)
     return *so;
 }
 
+// A^T digit planes of the packed tensor (part of the tensor upload; redone when the tensor or the
+// slice count changes).
 template <int S>
 static void prepare_tensor(Plan& p, SplitOperand& so, int N)
 {
-    if (so.dig[N] && so.dig_src[N] == p.d_tensor[N]) return;
-    const int n = p.n;
+    if (so.at[N] && so.at_src[N] == p.d_tensor[N]) return;
     const int64_t P = p.packed_count[N];
-    cudaFree(so.dig[N]);
-    cudaFree(so.dexp[N]);
-    NPF_CUDA(cudaMalloc(&so.dig[N], (size_t)n * P * 16));
-    NPF_CUDA(cudaMalloc(&so.dexp[N], 256 * sizeof(int)));
-    std::vector<int> none(256, EXP_NONE);
-    NPF_CUDA(cudaMemcpy(so.dexp[N], none.data(), 256 * sizeof(int), cudaMemcpyHostToDevice));
+    const int64_t rows = (P + NP - 1) / NP * NP;
+    cudaFree(so.at[N]);
+    cudaFree(so.at_e[N]);
+    NPF_CUDA(cudaMalloc(&so.at[N], (size_t)S * rows * NP * 2));
+    NPF_CUDA(cudaMalloc(&so.at_e[N], (size_t)rows * sizeof(int)));
+    NPF_CUDA(cudaMemsetAsync(so.at[N], 0, (size_t)S * rows * NP * 2, p.stream));
     {
-        LaunchScope ls(&p.prof, "split_tensor_exponents", p.stream);
-        k_row_exp<<<n, 256, 0, p.stream>>>(p.d_tensor[N], P, n, so.dexp[N]);
+        LaunchScope ls(&p.prof, "split_prepare_tensor", p.stream);
+        k_prep_at<S><<<(unsigned)((P + 7) / 8), 256, 0, p.stream>>>(p.d_tensor[N], P, p.n, so.at[N],
+                                                                    rows * NP, so.at_e[N]);
         NPF_CUDA(cudaGetLastError());
     }
-    {
-        LaunchScope ls(&p.prof, "split_slice_tensor", p.stream);
-        k_slice_packed<S><<<4096, 256, 0, p.stream>>>(p.d_tensor[N], P, n, so.dexp[N], so.dig[N]);
-        NPF_CUDA(cudaGetLastError());
-    }
-    so.dig_src[N] = p.d_tensor[N];
+    so.at_rows[N] = rows;
+    so.at_src[N] = p.d_tensor[N];
 }
 
-// Device memory of the split pipeline for one order:
-//   T buffers: 2 x cur x NP^N complex x S planes x 2 bytes x 2 (Re, Im)  [+ exponents]
-//   expansion: jc x NP^N x S x 2 bytes
-struct SplitBuffers {
-    __nv_bfloat16* T[2];
-    int* E[2];
-    __nv_bfloat16* X;
-    int cur, jc;
-    int64_t t_rows;       // operand rows per buffer (cur * NP^(N-1))
-    int64_t x_rows;       // rows of the expanded first operand (jc * NP^(N-1))
-};
-
-static SplitBuffers plan_buffers(Plan& p, int N, int S, int want_cur)
+void split_prepare_tensor(Plan& p, int N)
 {
-    const int64_t npN1 = ipow64(NP, N - 1);
-    const size_t per_cur = 2 * ((size_t)npN1 * KP * 2 * S + (size_t)npN1 * 4) + 1024;
-    const size_t per_j = (size_t)npN1 * NP * 2 * S;
-    const size_t budget = effective_budget(p);
-    int jc = (int)std::min<size_t>(16, std::max<size_t>(1, budget / 8 / per_j));
-    jc = std::min(jc, p.n);
-    if ((size_t)jc * per_j > budget) fail(NPF_ERR_OOM, "budget too small for one expansion chunk");
-    int cur = (int)std::min<size_t>((size_t)want_cur, (budget - (size_t)jc * per_j) / per_cur);
-    if (cur < 1) fail(NPF_ERR_OOM, "memory budget too small for one output-index batch");
-    SplitBuffers b{};
-    b.cur = cur;
-    b.jc = jc;
-    b.t_rows = (int64_t)cur * npN1;
-    b.x_rows = (int64_t)jc * npN1;
-    const size_t tbytes = (size_t)b.t_rows * KP * 2 * S;
-    const size_t ebytes = (size_t)b.t_rows * 4;
-    const size_t xbytes = (size_t)b.x_rows * NP * 2 * S;
-    p.arena.reserve(2 * (tbytes + ebytes + 256) + xbytes + 256);
-    uint8_t* base = (uint8_t*)p.arena.base;
-    auto take = [&](size_t bytes) { uint8_t* r = base; base += (bytes + 255) & ~(size_t)255; return r; };
-    b.T[0] = (__nv_bfloat16*)take(tbytes);
-    b.T[1] = (__nv_bfloat16*)take(tbytes);
-    b.E[0] = (int*)take(ebytes);
-    b.E[1] = (int*)take(ebytes);
-    b.X = (__nv_bfloat16*)take(xbytes);
-    return b;
+    if (p.precision == NPF_PREC_FP64 || N > 4 || p.n > NP) return;
+    SplitOperand& so = prepare(p);
+    so.at_src[N] = nullptr;   // the tensor's contents changed: always redo
+    switch (so.S) {
+    case 2: prepare_tensor<2>(p, so, N); break;
+    case 3: prepare_tensor<3>(p, so, N); break;
+    case 4: prepare_tensor<4>(p, so, N); break;
+    case 5: prepare_tensor<5>(p, so, N); break;
+    case 6: prepare_tensor<6>(p, so, N); break;
+    default: break;
+    }
 }
 
 template <int S, int MODE>
 static void launch_rows(Plan& p, const char* name, const CUtensorMap& tA, const CUtensorMap& tB,
-                        RowArgs a)
+                        const RowArgs& a)
 {
     LaunchScope ls(&p.prof, name, p.stream);
-    k_ozaki_rows<S, MODE><<<(unsigned)a.num_tiles, 192, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+    k_rows<S, MODE><<<(unsigned)a.num_tiles, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
     NPF_CUDA(cudaGetLastError());
 }
 
 static double factorial(int N) { double f = 1; for (int t = 2; t <= N; ++t) f *= t; return f; }
 
-// The whole order-N pipeline for output-index batches; for a slab request (prefix != nullptr)
-// only the batch holding prefix[0] runs and h is stored in FP64 for extraction.
+// Device memory of one order: S (FP64, n x P), records (n x P x 32 B), and per i of a batch two
+// operand buffers of NP^(N-1) rows x 256 K' x S planes (BF16) plus exponents.
 template <int S>
 static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
 {
@@ -946,156 +1050,132 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     NPF_CUDA(cudaMemsetAsync(so.err, 0, sizeof(int), p.stream));
     const int n = p.n;
     const int64_t P = p.packed_count[N];
+    const int64_t Prows = so.at_rows[N];
     const int64_t npN1 = ipow64(NP, N - 1);
     const bool slab = prefix != nullptr;
-    SplitBuffers B = plan_buffers(p, N, S, slab ? 1 : n);
-    double2* hslab = nullptr;
-    if (slab) {
-        NPF_CUDA(cudaMalloc(&hslab, (size_t)npN1 * NP * sizeof(double2)));
-    } else {
-        launch_zero(p, d_out, (int64_t)n * n);
-    }
+
+    // ---- memory plan (Algorithm 1's rule on the upper-index space)
+    const size_t s_bytes = (size_t)n * Prows * sizeof(double2);
+    const size_t rec_bytes = (size_t)n * P * 32;
+    const size_t per_i = 2 * ((size_t)npN1 * KP * 2 * S + (size_t)npN1 * 4) + 4096;
+    const size_t budget = effective_budget(p);
+    if (s_bytes + rec_bytes + per_i > budget)
+        fail(NPF_ERR_OOM, "memory budget too small for one upper-index batch");
+    const int ib = (int)std::min<size_t>((size_t)n, (budget - s_bytes - rec_bytes) / per_i);
+    const int64_t t_rows = (int64_t)ib * npN1;
+    const size_t tbytes = (size_t)t_rows * KP * 2 * S;
+    const size_t ebytes = (size_t)t_rows * 4;
+    p.arena.reserve(s_bytes + rec_bytes + 2 * (tbytes + ebytes) + 8 * 256 + 1024);
+    uint8_t* base = (uint8_t*)p.arena.base;
+    auto take = [&](size_t bytes) { uint8_t* r = base; base += (bytes + 255) & ~(size_t)255; return r; };
+    double2* Sd = (double2*)take(s_bytes);
+    uint4* rec = (uint4*)take(rec_bytes);
+    int* sE = (int*)take(256 * sizeof(int));
+    __nv_bfloat16* T[2] = {(__nv_bfloat16*)take(tbytes), (__nv_bfloat16*)take(tbytes)};
+    int* E[2] = {(int*)take(ebytes), (int*)take(ebytes)};
+
+    if (!slab) launch_zero(p, d_out, (int64_t)n * n);
+
     const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, 64);
-    const CUtensorMap tPsi = make_tmap(so.psi, KP, (int64_t)S * 512, 64);
+    const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, 64);
     const CUtensorMap tRed = make_tmap(so.red, KP, (int64_t)S * 512, 128);
-    const CUtensorMap tX = make_tmap(B.X, NP, (int64_t)S * B.x_rows, 128);
-    const CUtensorMap tT0 = make_tmap(B.T[0], KP, (int64_t)S * B.t_rows, 128);
-    const CUtensorMap tT1 = make_tmap(B.T[1], KP, (int64_t)S * B.t_rows, 128);
-    const CUtensorMap tTB0 = make_tmap(B.T[0], KP, (int64_t)S * B.t_rows, RedCfg<S>::BNC);
-    const CUtensorMap tTB1 = make_tmap(B.T[1], KP, (int64_t)S * B.t_rows, RedCfg<S>::BNC);
+    const CUtensorMap tAT = make_tmap(so.at[N], NP, (int64_t)S * Prows, 128);
+    const CUtensorMap tT0 = make_tmap(T[0], KP, (int64_t)S * t_rows, 128);
+    const CUtensorMap tT1 = make_tmap(T[1], KP, (int64_t)S * t_rows, 128);
+    const CUtensorMap tTB0 = make_tmap(T[0], KP, (int64_t)S * t_rows, RedCfg<S>::BNC);
+    const CUtensorMap tTB1 = make_tmap(T[1], KP, (int64_t)S * t_rows, RedCfg<S>::BNC);
     const CUtensorMap* tT[2] = {&tT0, &tT1};
     const CUtensorMap* tTB[2] = {&tTB0, &tTB1};
 
-    RowArgs base{};
-    base.eb = so.phi_e;
-    base.lam = p.d_lam;
-    base.n = n;
-    base.N = N;
-    base.invfact = 1.0 / factorial(N);
-    base.eps = p.eps;
-    base.divide = p.divide;
-    base.err = so.err;
+    RowArgs base0{};
+    base0.n = n;
+    base0.N = N;
+    base0.lam = p.d_lam;
+    base0.invfact = 1.0 / factorial(N);
+    base0.eps = p.eps;
+    base0.divide = p.divide;
+    base0.err = so.err;
+    base0.bnc = 64;
+    base0.ncol_tiles = 2;
+    if (slab)
+        for (int m = 0; m < N - 1; ++m) base0.pre[m] = prefix[m];
 
-    const int b_first = slab ? prefix[0] : 0;
-    const int b_last = slab ? prefix[0] + 1 : n;
-    for (int b0 = b_first; b0 < b_last; b0 += B.cur) {
-        const int cur = std::min(B.cur, b_last - b0);
-        // ---- first contraction: rows (j, a_1..a_{N-1}), K = a_N, new index pb
-        for (int j0 = 0; j0 < NP; j0 += B.jc) {
-            const int jc = std::min(B.jc, NP - j0);
-            {
-                LaunchScope ls(&p.prof, "split_expand_first", p.stream);
-                k_expand_first<S><<<8192, 256, 0, p.stream>>>(so.dig[N], P, n, N, j0, jc, p.d_cnt,
-                                                              B.X, B.x_rows * NP);
-                NPF_CUDA(cudaGetLastError());
-            }
-            RowArgs a = base;
-            a.a_rows = (int)B.x_rows;
-            a.kch = NP / BK;
-            a.ea = so.dexp[N];
-            a.ea_shift = 7 * (N - 1);
-            a.ea_off = 0;
-            a.bcol0 = b0;
-            a.bnc = std::min(64, (cur + 7) / 8 * 8);
-            a.ncol_tiles = (cur + a.bnc - 1) / a.bnc;
-            a.ncols_valid = cur;
-            a.num_tiles = (int64_t)jc * npN1 / NP * a.ncol_tiles;
-            a.o_base = (int64_t)j0 * npN1;
-            a.R = (int64_t)NP * npN1;
-            a.npc = cur;
-            a.out_planes = B.T[0];
-            a.out_plane_stride = B.t_rows * KP;
-            a.out_exp = B.E[0];
-            const CUtensorMap tPhiFirst = make_tmap(so.phi, KP, (int64_t)S * 512, a.bnc);
-            launch_rows<S, EPI_SLICE>(p, "split_first_contraction", tX, tPhiFirst, a);
-        }
-        // ---- mode products on the innermost index, N-1 times: [pb][p][rest]
-        int cb = 0;
+    // ---- P1: S[i][Q] = sum_j psi_ij A^j_Q (rows Q, real K = j)
+    {
+        RowArgs a = base0;
+        a.a_rows = (int)Prows;
+        a.kch = NP / BK;
+        a.ea = so.at_e[N];
+        a.ea_shift = 0;
+        a.eb = so.psir_e;
+        a.num_tiles = Prows / NP * 2;
+        a.c = 0;
+        a.R = Prows;
+        a.npc = n;
+        a.out_f64 = Sd;
+        a.ld_f64 = Prows;
+        launch_rows<S, EPI_F64T>(p, "split_upper_contraction", tAT, tPsiR, a);
+    }
+    {
+        LaunchScope ls(&p.prof, "split_s_records", p.stream);
+        k_s_exp<<<n, 256, 0, p.stream>>>(Sd, Prows, P, sE);
+        k_s_records<S><<<4096, 256, 0, p.stream>>>(Sd, Prows, P, n, sE, rec);
+        NPF_CUDA(cudaGetLastError());
+    }
+
+    for (int i0 = 0; i0 < n; i0 += ib) {
+        const int cur = std::min(ib, n - i0);
         const int64_t rows = (int64_t)cur * npN1;
-        for (int m = 2; m <= N; ++m) {
-            RowArgs a = base;
-            a.a_rows = (int)B.t_rows;
-            a.kch = KP / BK;
-            a.ea = B.E[cb];
-            a.ea_shift = 0;
-            a.bcol0 = 0;
-            a.bnc = 64;
-            a.ncol_tiles = 2;
-            a.ncols_valid = NP;
-            a.num_tiles = rows / NP * 2;
-            a.o_base = 0;
-            a.R = npN1;
-            a.npc = NP;
-            a.out_planes = B.T[cb ^ 1];
-            a.out_plane_stride = B.t_rows * KP;
-            a.out_exp = B.E[cb ^ 1];
-            launch_rows<S, EPI_SLICE>(p, "split_mode_product", *tT[cb], tPhi, a);
-            cb ^= 1;
-        }
-        // ---- upper index with Psi, 1/N!, resonance divide: [pb][i][p_1..p_{N-1}]
         {
-            RowArgs a = base;
-            a.a_rows = (int)B.t_rows;
-            a.kch = KP / BK;
-            a.ea = B.E[cb];
-            a.ea_shift = 0;
-            a.eb = so.psi_e;
-            a.bcol0 = 0;
-            a.bnc = 64;
-            a.ncol_tiles = 2;
-            a.ncols_valid = NP;
-            a.num_tiles = rows / NP * 2;
-            a.o_base = 0;
-            a.R = npN1;
-            a.npc = NP;
-            a.b0 = b0;
-            a.out_planes = B.T[cb ^ 1];
-            a.out_plane_stride = B.t_rows * KP;
-            a.out_exp = B.E[cb ^ 1];
-            if (slab) {
-                a.out_f64 = hslab;
-                launch_rows<S, EPI_F64>(p, "split_psi_divide", *tT[cb], tPsi, a);
-            } else {
-                launch_rows<S, EPI_DIVIDE>(p, "split_psi_divide", *tT[cb], tPsi, a);
-            }
-            cb ^= 1;
-        }
-        if (slab) break;
-        // ---- reduction with the Khatri-Rao weights into Psi_N
-        {
-            RedArgs r{};
-            r.kch = KP / BK;
-            r.ea = so.red_e;
-            r.b_rows = (int)B.t_rows;
-            r.eb = B.E[cb];
-            r.bnc = RedCfg<S>::BNC;
-            r.num_tiles = rows / RedCfg<S>::BNC;
-            r.psi_df = so.psi_df;
-            r.V = p.d_V;
-            r.n = n;
-            r.N = N;
-            r.b0 = b0;
-            r.psiN = d_out;
-            r.err = so.err;
-            LaunchScope ls(&p.prof, "split_reduce", p.stream);
-            k_ozaki_reduce<S><<<(unsigned)r.num_tiles, 192, RedCfg<S>::SMEM, p.stream>>>(
-                tRed, *tTB[cb], r);
+            LaunchScope ls(&p.prof, "split_expand", p.stream);
+            k_expand<S><<<8192, 256, 0, p.stream>>>(rec, P, n, N, i0, cur, p.d_cnt,
+                                                    (uint32_t*)T[0], t_rows * (KP / 2));
             NPF_CUDA(cudaGetLastError());
         }
-    }
-    if (slab) {
-        // h[i][q] = hslab[(p_1' .. p_{N-1}') row][i] with row = (prefix[1..N-2], q) base NP
-        std::vector<double2> h((size_t)npN1 * NP);
-        NPF_CUDA(cudaMemcpyAsync(h.data(), hslab, h.size() * sizeof(double2), cudaMemcpyDeviceToHost,
-                                 p.stream));
-        NPF_CUDA(cudaStreamSynchronize(p.stream));
-        cudaFree(hslab);
-        std::vector<double2> out((size_t)n * n);
-        int64_t rbase = 0;
-        for (int m = 1; m < N - 1; ++m) rbase = rbase * NP + prefix[m];
-        for (int q = 0; q < n; ++q)
-            for (int i = 0; i < n; ++i) out[(size_t)i * n + q] = h[(size_t)(rbase * NP + q) * NP + i];
-        NPF_CUDA(cudaMemcpy(d_out, out.data(), out.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        int cb = 0;
+        for (int c = 1; c <= N; ++c) {
+            RowArgs a = base0;
+            a.a_rows = (int)t_rows;
+            a.kch = KP / BK;
+            a.ea = c == 1 ? sE + i0 : E[cb];
+            a.ea_shift = c == 1 ? 7 * (N - 1) : 0;
+            a.eb = so.phi_e;
+            a.num_tiles = rows / NP * 2;
+            a.c = c;
+            a.R = npN1;
+            a.npc = NP;
+            a.i0 = i0;
+            a.out_planes = T[cb ^ 1];
+            a.out_plane_stride = t_rows * KP;
+            a.out_exp = E[cb ^ 1];
+            if (c < N) {
+                launch_rows<S, EPI_SLICE>(p, "split_mode_product", *tT[cb], tPhi, a);
+            } else if (slab) {
+                a.out_f64 = d_out;
+                launch_rows<S, EPI_SLAB>(p, "split_mode_divide", *tT[cb], tPhi, a);
+            } else {
+                launch_rows<S, EPI_DIVIDE>(p, "split_mode_divide", *tT[cb], tPhi, a);
+            }
+            cb ^= 1;
+        }
+        if (slab) continue;
+        RedArgs r{};
+        r.kch = KP / BK;
+        r.ea = so.red_e;
+        r.b_rows = (int)t_rows;
+        r.eb = E[cb];
+        r.bnc = RedCfg<S>::BNC;
+        r.num_tiles = rows / RedCfg<S>::BNC;
+        r.psi_df = so.psi_df;
+        r.V = p.d_V;
+        r.n = n;
+        r.N = N;
+        r.i0 = i0;
+        r.psiN = d_out;
+        r.err = so.err;
+        LaunchScope ls(&p.prof, "split_reduce", p.stream);
+        k_reduce<S><<<(unsigned)r.num_tiles, 192, RedCfg<S>::SMEM, p.stream>>>(tRed, *tTB[cb], r);
+        NPF_CUDA(cudaGetLastError());
     }
     int herr = 0;
     NPF_CUDA(cudaMemcpyAsync(&herr, so.err, sizeof(int), cudaMemcpyDeviceToHost, p.stream));
@@ -1103,22 +1183,16 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     if (herr) fail(NPF_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
 }
 
-template <int S>
-static void split_dispatch(Plan& p, int N, double2* d_out, const int* prefix)
-{
-    split_run<S>(p, N, d_out, prefix);
-}
-
 static void split_any(Plan& p, int N, double2* d_out, const int* prefix)
 {
     if (N < 2) fail(NPF_ERR_ARG, "order must be >= 2");
     if (N > 4) fail(NPF_ERR_UNSUPPORTED, "the tensor-core path supports orders <= 4 (use NPF_PREC_FP64)");
     switch (default_slices(p)) {
-    case 2: split_dispatch<2>(p, N, d_out, prefix); break;
-    case 3: split_dispatch<3>(p, N, d_out, prefix); break;
-    case 4: split_dispatch<4>(p, N, d_out, prefix); break;
-    case 5: split_dispatch<5>(p, N, d_out, prefix); break;
-    case 6: split_dispatch<6>(p, N, d_out, prefix); break;
+    case 2: split_run<2>(p, N, d_out, prefix); break;
+    case 3: split_run<3>(p, N, d_out, prefix); break;
+    case 4: split_run<4>(p, N, d_out, prefix); break;
+    case 5: split_run<5>(p, N, d_out, prefix); break;
+    case 6: split_run<6>(p, N, d_out, prefix); break;
     default: fail(NPF_ERR_UNSUPPORTED, "slices must be in [2, 6] on the tensor-core path");
     }
 }

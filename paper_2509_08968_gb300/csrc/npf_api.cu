@@ -172,6 +172,7 @@ int npf_set_tensor(npf_handle* h, int order, const double* coeffs)
         const size_t bytes = (size_t)p.n * p.packed_count[order] * sizeof(double);
         if (!p.d_tensor[order]) NPF_CUDA(cudaMalloc(&p.d_tensor[order], bytes));
         copy_in(p.d_tensor[order], coeffs, bytes, p.stream);
+        npf::split_prepare_tensor(p, order);   // tensor-core forms: digit planes of the upload
         sync(p);
     });
 }

@@ -114,6 +114,7 @@ void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out /* h [n][n] */)
 void split_term(Plan& p, int N, double2* d_out);
 void split_slab(Plan& p, int N, const int* prefix, double2* d_out);
 void split_release(Plan& p);
+void split_prepare_tensor(Plan& p, int N);   // digit planes of a newly uploaded tensor
 
 // ----------------------------------------------------------------------------------------
 // Small shared kernels (k_common.cu).
