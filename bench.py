@@ -229,18 +229,23 @@ def main():
 
     # ---- roofline of the dominant kernel (live CUDA-event durations of the timed steps)
     peaks, src = measured_peaks()
-    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None
-    if top:
-        name, (cnt, tot_ms) = top
-        avg_ms = tot_ms / max(1, cnt)
-        fl = algorithmic_flops_per_launch(name, n, prof, args.precision)
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        if fl is not None:
-            achieved = fl / (avg_ms * 1e-3) / 1e12
-            roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"bf16 sustained ({src})",
+    if prof:
+        name, (cnt, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+        work, kind = algorithmic_work_per_step(name, n, args.precision)
+        if work is not None:
+            per_launch = work * args.steps / cnt
+            avg_ms = tot_ms / cnt
+            if kind == "flops":
+                peak = peaks.get("bf16_tflops_sustained", 1700.0)
+                achieved = per_launch / (avg_ms * 1e-3) / 1e12
+                bound, unit, psrc = "tensor", "TFLOP/s", f"bf16 sustained ({src})"
+            else:
+                peak = peaks.get("hbm_gbs", 6800.0)
+                achieved = per_launch / (avg_ms * 1e-3) / 1e9
+                bound, unit, psrc = "hbm", "GB/s", f"hbm copy ({src})"
+            roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
+                    "unit": unit, "frac": achieved / peak, "traffic": None, "peak_source": psrc,
                     "launches": cnt, "avg_ms": avg_ms,
                     "share": tot_ms / sum(v[1] for v in prof.values())}
 
@@ -298,32 +303,44 @@ def main():
     return 0
 
 
-PAIRS = {"split_bf16": 15, "fp32": 6, "fp64": 1}
+PAIRS = {"split_bf16": 21, "fp32": 6, "fp64": 1}     # BF16 slice pairs s + t < S (S = 6 / 3)
+SLICES = {"split_bf16": 6, "fp32": 3, "fp64": 0}
 
 
-def algorithmic_flops_per_launch(name, n, prof, precision):
-    """Useful (unpadded) tensor flops of one launch of the named kernel, averaged over the
-    step: each complex multiply-add over the K dimension is 4 real products on 2 real outputs
-    -> 8 real flops per (entry, k), times the slice pairs executed on the tensor cores."""
+def algorithmic_work_per_step(name, n, precision):
+    """Algorithmic work of every launch of `name` in one step, as (amount, kind).
+
+    Tensor kernels (kind "flops"): executed BF16 tensor flops of the work the symmetric method
+    needs -- only non-decreasing lower-index tuples are formed, indices unpadded (n, not 128);
+    a complex multiply-add over K is 8 real flops, times the slice pairs. Per order N with
+    C(m, r) = binomial:
+      split_upper_contraction : C(n+N-1,N) packed tuples x n (i) x n (j) x 4 (real x complex)
+      split_mode_product      : sum_{c=1..N-1} n (i) x C(n+c-1,c) (sorted p's) x n^(N-c) (a's)
+                                x n (K) x 8
+      split_mode_divide       : n (i) x C(n+N-1,N) x n (K) x 8
+      split_reduce            : n (i) x C(n+N-2,N-1) (rows) x n (k) x n (K) x 8
+    Memory kernels (kind "bytes"): split_expand gathers one 32-byte digit record and writes
+    S planes x 4 bytes per dense operand entry: n (i) x n^N x (32 + 4 S).
+    """
+    from math import comb
     pairs = PAIRS[precision]
-    cnt = prof[name][0]
-    steps_entries = 0
-    if name == "split_mode_product":
-        # one launch per (order N, batch, mode m); every mode product of order N touches
-        # all n^(N+1) complex entries with K = n; total over a step: sum_N (N-1) n^(N+2)
-        tot = sum((N - 1) * n ** (N + 2) for N in ORDERS) * 8 * pairs
-    elif name == "split_first_contraction":
-        tot = sum(n ** (N + 2) for N in ORDERS) * 4 * pairs   # real x complex
-    elif name == "split_psi_divide":
-        tot = sum(n ** (N + 2) for N in ORDERS) * 8 * pairs
-    elif name == "split_reduce":
-        tot = sum(n ** (N + 2) for N in ORDERS) * 8 * pairs
-    elif name == "fp64_mode_product":
-        tot = sum((N - 1) * n ** (N + 2) for N in ORDERS) * 8
-    else:
-        return None
-    steps = prof.get("npf_finish", (1, 0))[0] or 1
-    return tot * steps / cnt
+    tot = 0
+    for N in ORDERS:
+        if name == "split_upper_contraction":
+            tot += comb(n + N - 1, N) * n * n * 4 * pairs
+        elif name == "split_mode_product":
+            tot += sum(n * comb(n + c - 1, c) * n ** (N - c) * n * 8 for c in range(1, N)) * pairs
+        elif name == "split_mode_divide":
+            tot += n * comb(n + N - 1, N) * n * 8 * pairs
+        elif name == "split_reduce":
+            tot += n * comb(n + N - 2, N - 1) * n * n * 8 * pairs
+        elif name == "split_expand":
+            tot += n * n ** N * (32 + 4 * SLICES[precision])
+        elif name == "fp64_mode_product":
+            tot += (N - 1) * n ** (N + 2) * 8
+        else:
+            return None, None
+    return tot, ("bytes" if name == "split_expand" else "flops")
 
 
 if __name__ == "__main__":
