@@ -158,6 +158,8 @@ def main():
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile-n", type=int, default=0,
+                    help="complex columns per tensor-core tile (16/32/64; 0 = library default)")
     ap.add_argument("--workload", default="n120", choices=list(WORKLOADS),
                     help="n120: the measured configuration; the others are small cases for "
                          "profiler captures")
@@ -185,6 +187,8 @@ def main():
     stream = torch.cuda.current_stream()
     plan = npf.Plan(sysm.lam, sysm.U, sysm.V, max(ORDERS), precision=args.precision,
                     stream=stream.cuda_stream)
+    if args.tile_n:
+        plan.set_option(npf.OPT_TILE_N, args.tile_n)
     dev_tensors = {N: torch.from_numpy(sysm.tensors[N]).cuda() for N in ORDERS}
     for N in ORDERS:
         plan.set_tensor(N, dev_tensors[N])

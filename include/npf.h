@@ -73,7 +73,8 @@ enum npf_option {
                                debugging switch behind the collapse identity
                                sum_p C^i_p prod_m psi_{p_m k} = (1/N!) sum_j psi_ij A^j_{k..k}. */
     NPF_OPT_MEM_BUDGET = 5, /* bytes of device memory for intermediates; 0 = 80% of free memory. */
-    NPF_OPT_PROFILE = 6     /* 1: time each kernel launch with CUDA events (npf_get_profile). */
+    NPF_OPT_PROFILE = 6,    /* 1: time each kernel launch with CUDA events (npf_get_profile). */
+    NPF_OPT_TILE_N = 7      /* complex columns per tensor-core tile: 16, 32 or 64 (default 64). */
 };
 
 /* Arithmetic of the dense contraction. The denominators, the divide, the Psi_N sums and the

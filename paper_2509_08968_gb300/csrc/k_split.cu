@@ -39,6 +39,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -86,19 +88,51 @@ __device__ __forceinline__ uint32_t digit_bf16(int d, int s)
     return __float_as_uint((float)d * pow2f(-8 * s)) >> 16;
 }
 
-// Balanced base-256 digits of W, packed as (Re, Im) BF16 pairs per plane.
+// Balanced base-256 digits of W (|W| <= 2^(7 + 8(S-1))), packed as (Re, Im) BF16 pairs per
+// plane: plane s holds d_s * 2^(-8 s), d_0 the most significant digit. Adding 128 to every lower
+// digit (the constant OFF) turns them into plain bytes u = d + 128 in [0, 255] with no borrows,
+// and the top digit is the arithmetic shift of the sum. A byte becomes the float d * 2^(-8 s)
+// exactly through the bit pattern of 2^23 + u and one fused multiply-add.
+template <int S>
+struct DigitOff {
+    static constexpr long long value = (DigitOff<S - 1>::value << 8) | 128;
+};
+template <>
+struct DigitOff<0> { static constexpr long long value = 0; };
+
+__device__ __forceinline__ float byte_to_digit(uint32_t u, int s)
+{
+    // (2^23 + u) * 2^(-8s) - (2^23 + 128) * 2^(-8s) = (u - 128) * 2^(-8s), exact
+    const float sc = pow2f(-8 * s);
+    return fmaf(__uint_as_float(0x4B000000u | u), sc, -8388736.0f * sc);
+}
+
 template <int S>
 __device__ __forceinline__ void digit_pairs(long long Wr, long long Wi, uint32_t (&out)[S])
 {
+    constexpr long long OFF = DigitOff<S - 1>::value;   // 128 in each of the S-1 lower bytes
+    const unsigned long long ur = (unsigned long long)(Wr + OFF);
+    const unsigned long long ui = (unsigned long long)(Wi + OFF);
+    const uint32_t rlo = (uint32_t)ur, rhi = (uint32_t)(ur >> 32);
+    const uint32_t ilo = (uint32_t)ui, ihi = (uint32_t)(ui >> 32);
 #pragma unroll
-    for (int s = S - 1; s >= 1; --s) {
-        const int lr = (int)((Wr + 128) & 255) - 128;
-        const int li = (int)((Wi + 128) & 255) - 128;
-        out[s] = digit_bf16(lr, s) | (digit_bf16(li, s) << 16);
-        Wr = (Wr - lr) >> 8;
-        Wi = (Wi - li) >> 8;
+    for (int s = 0; s < S; ++s) {
+        const int k = S - 1 - s;   // byte position from the least significant end
+        float fr, fi;
+        if (s == 0) {
+            const long long tr = (long long)(Wr + OFF) >> (8 * k);
+            const long long ti = (long long)(Wi + OFF) >> (8 * k);
+            fr = byte_to_digit((uint32_t)(tr + 128), 0);
+            fi = byte_to_digit((uint32_t)(ti + 128), 0);
+        } else {
+            const uint32_t br = k < 4 ? (rlo >> (8 * k)) & 255u : (rhi >> (8 * (k - 4))) & 255u;
+            const uint32_t bi = k < 4 ? (ilo >> (8 * k)) & 255u : (ihi >> (8 * (k - 4))) & 255u;
+            fr = byte_to_digit(br, s);
+            fi = byte_to_digit(bi, s);
+        }
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(fr, fi);
+        out[s] = *reinterpret_cast<const uint32_t*>(&h2);
     }
-    out[0] = digit_bf16((int)Wr, 0) | (digit_bf16((int)Wi, 0) << 16);
 }
 
 struct dfl { float hi, lo; };
@@ -162,11 +196,16 @@ __device__ __forceinline__ void load_levels(uint32_t taddr, int stride, uint32_t
 __host__ __device__ constexpr int64_t ipow_np(int e) { return e <= 0 ? 1 : NP * ipow_np(e - 1); }
 
 // digits of r (N-1 digits base NP, most significant first) into d[0..N-2]
-__device__ __forceinline__ void row_digits(int64_t r, int nd, int* d)
+__device__ __forceinline__ void row_digits(int64_t r, int nd, int (&d)[8])
 {
-    for (int m = nd - 1; m >= 0; --m) {
-        d[m] = (int)(r % NP);
-        r /= NP;
+#pragma unroll
+    for (int m = 7; m >= 0; --m) {   // unrolled with static indices: d stays in registers
+        if (m < nd) {
+            d[m] = (int)(r % NP);
+            r /= NP;
+        } else {
+            d[m] = 0;
+        }
     }
 }
 
@@ -219,8 +258,14 @@ __global__ void k_prep_at(const double* __restrict__ A, int64_t P, int n,
 // ---------------------------------------------------------------------------------------
 // Row-data GEMM: data rows on the M side (128 per tile), the fixed complex matrix on the N side
 // (bnc complex columns per tile -> 2*bnc real columns: Re block then Im block).
+//
+// A launch works on rows o = outer * R + r where r holds N-1 base-128 digits (most significant
+// first): `rp` leading lower output indices p followed by lower input indices a; the innermost
+// digit varies within a 128-row tile, the others are shared by the tile. The non-decreasing rule
+// (only p's in order, new column <= first p when `colmask`) and the padding (digits >= n) decide
+// which tiles run and which elements count.
 // ---------------------------------------------------------------------------------------
-enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3 };
+enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3, EPI_REDUCE = 4 };
 
 struct RowArgs {
     int a_rows;          // rows per plane in the A tensor map
@@ -232,23 +277,35 @@ struct RowArgs {
     int ncol_tiles;
     int64_t num_tiles;
     int N;               // order
-    int c;               // contraction index 1..N (0: upper-index contraction P1)
+    int digits;          // 1: r carries N-1 index digits (0 for the packed-tuple rows of P1)
+    int rp;              // leading p digits in r
+    int colmask;         // new column must be <= the first p
     int64_t R;           // rows per outer index (output layout [outer][q][r])
     int npc;             // extent of the new index in the output layout
     int n;
     __nv_bfloat16* out_planes;
     int64_t out_plane_stride;
     int* out_exp;
-    double2* out_f64;    // EPI_F64T: out[q * ld_f64 + o]; EPI_SLAB: out[i * n + q]
+    double2* out_f64;    // EPI_F64T: out[q * ld_f64 + o]; EPI_SLAB: out[i * n + q]; EPI_REDUCE: Psi_N
     int64_t ld_f64;
-    // EPI_DIVIDE / EPI_SLAB
+    // EPI_DIVIDE / EPI_SLAB / EPI_REDUCE
     const double2* lam;
+    const double2* V;        // psi_{p k} at p*n + k
+    const float4* psi_df;    // the same as double-float
     int i0;
     double invfact, eps;
     int divide;
-    int pre[8];          // EPI_SLAB: the requested sorted prefix (N-1 indices)
+    int pre[8];          // EPI_SLAB: the requested prefix (N-1 indices)
     int* err;
+    unsigned long long* trace;   // optional per-CTA phase timestamps [tile][6] (nullptr: off)
 };
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 template <int S>
 struct RowCfg {
@@ -260,21 +317,21 @@ struct RowCfg {
     static_assert(STAGES * STAGE_BYTES >= 128 * 64 * 16, "epilogue staging must fit");
 };
 
-// Is the non-decreasing order of the row's p indices (and the new column) broken?
-// For contraction c the row r = (p_{N-c+2}..p_N, a_1..a_{N-c}) carries c-1 p's.
 __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_local, int ct)
 {
-    if (a.c < 2) return false;
-    const int64_t r = row0_local % a.R;
+    if (ct * a.bnc >= a.n) return true;                    // every column is padding
+    if (!a.digits) return false;
     int d[8];
-    row_digits(r, a.N - 1, d);
-    const int np = a.c - 1;                       // p's in the row
-    const int shared = (a.c < a.N) ? np : np - 1; // p's constant over the tile
-    for (int m = 1; m < shared; ++m)
-        if (d[m - 1] > d[m]) return true;
-    for (int m = 0; m < shared; ++m)
-        if (d[m] >= a.n) return true;                     // padding index: all zero
-    if (shared >= 1 && ct * a.bnc > d[0]) return true;   // every new index > first p
+    row_digits(row0_local % a.R, a.N - 1, d);
+    const int nd = a.N - 1;
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        if (m + 1 >= nd) break;                            // shared digits: 0 .. nd-2
+        if (d[m] >= a.n) return true;                      // padding index: rows are zero
+        if (m >= 1 && m < a.rp && d[m - 1] > d[m]) return true;
+    }
+    const bool first_shared = a.rp >= 1 && nd >= 2;
+    if (a.colmask && first_shared && ct * a.bnc > d[0]) return true;
     return false;
 }
 
@@ -291,7 +348,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     uint64_t* empty = full + C::STAGES;
     uint64_t* acc_full = empty + C::STAGES;
     uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
-    int* colE = (int*)(tmem_slot + 4);  // 64 ints
+    int* colE = (int*)(tmem_slot + 4);   // 64 ints: column exponent keys
+    int* colEb = colE + 64;              // 64 ints: fixed-matrix column exponents
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t tile = blockIdx.x;
@@ -299,6 +357,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     const int64_t rt = tile / args.ncol_tiles;
     const int64_t row0 = rt * NP;
     if (tile_skipped(args, row0, ct)) return;   // uniform over the CTA
+    unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
+    if (trc && threadIdx.x == 0) trc[0] = global_ns();
     const int bnr = 2 * args.bnc;
     const uint32_t b_bytes_tile = (uint32_t)bnr * BK * 2;
 
@@ -316,11 +376,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         tc::tmem_alloc(tmem_slot, TMEM_COLS);
         tc::tmem_relinquish();
     }
-    if (threadIdx.x >= 64 && threadIdx.x < 128) colE[threadIdx.x - 64] = 0;
+    if (threadIdx.x >= 64 && threadIdx.x < 128) {
+        colE[threadIdx.x - 64] = 0;
+        colEb[threadIdx.x - 64] = args.eb[ct * args.bnc + threadIdx.x - 64];
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
+    if (trc && threadIdx.x == 0) trc[1] = global_ns();
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
@@ -351,6 +415,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             const uint32_t ph = (kc / C::STAGES) & 1;
             if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) break;
             tc::fence_after_sync();
+            if (trc && kc == 0) trc[2] = global_ns();   // first stage landed
             const uint32_t aBase = tc::smem_u32(stage_base + st * C::STAGE_BYTES);
             const uint32_t bBase = aBase + S * C::A_TILE;
 #pragma unroll
@@ -378,6 +443,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
         const bool ok = tc::mbar_wait(acc_full, 0, args.err, kErrTimeout);
         tc::fence_after_sync();
+        if (trc && threadIdx.x == 64) trc[3] = global_ns();   // accumulators complete
         const int bnc = args.bnc;
         const int cols = bnc / 2;
         const int cbeg = half * cols;
@@ -389,31 +455,46 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         const int64_t rperq = args.R / NP;
         const int N = args.N, n = args.n;
 
-        // row p's (c >= 1): digits of rr, the first c-1 are p's
+        // row digits: the first rp are p's (must be in order and < n), then a's (< n)
         int dg[8];
         row_digits(rr, N - 1, dg);
-        const int np_row = args.c >= 1 ? args.c - 1 : 0;
         bool row_ok = true;
-        for (int m = 1; m < np_row; ++m) row_ok &= dg[m - 1] <= dg[m];
-        for (int m = 0; m < np_row; ++m) row_ok &= dg[m] < n;
-        const int firstp = np_row >= 1 ? dg[0] : NP;
+        int firstp = NP;
+        if (args.digits) {
+#pragma unroll
+            for (int m = 0; m < 7; ++m) {
+                if (m < N - 1) {
+                    row_ok &= dg[m] < n;
+                    if (m >= 1 && m < args.rp) row_ok &= dg[m - 1] <= dg[m];
+                }
+            }
+            if (args.rp >= 1) firstp = dg[0];
+        }
 
-        // EPI_DIVIDE / EPI_SLAB: sigma of the row p's, multiplicity base and first run length
+        // EPI_DIVIDE / EPI_SLAB: sigma of the row p's minus lambda_i, multiplicity base and the
+        // length of the first run of equal p's
         double2 sigma = make_double2(0, 0);
         double mult_base = 1.0;
         int run1 = 1;
         if (MODE == EPI_DIVIDE || MODE == EPI_SLAB) {
+            const int np_row = args.rp;
             if (row_ok) {
-                for (int m = 0; m < np_row; ++m) sigma = cadd(sigma, args.lam[dg[m]]);
+#pragma unroll
+                for (int m = 0; m < 7; ++m)
+                    if (m < np_row) sigma = cadd(sigma, args.lam[dg[m]]);
                 sigma = csub(sigma, args.lam[args.i0 + (int)outer]);
             }
             double denom = 1.0;
             int run = 1;
-            for (int m = 1; m <= np_row; ++m) {
+            bool first_run = true;
+#pragma unroll
+            for (int m = 1; m < 8; ++m) {
+                if (m > np_row) break;
                 if (m < np_row && dg[m] == dg[m - 1]) {
                     ++run;
                 } else {
-                    if (m - run == 0) run1 = run;
+                    if (first_run) run1 = run;
+                    first_run = false;
                     for (int t = 2; t <= run; ++t) denom *= t;
                     run = 1;
                 }
@@ -424,9 +505,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         }
         long long* vbuf = (long long*)stage_base;     // [64 cols][128 rows][2] (pipeline drained)
         double2* hbuf = (double2*)stage_base;         // same storage, FP64 quotients
+        float4* gbuf = (float4*)stage_base;           // same storage, double-float products
 
         if (ok) {
-            // pass 1: recombine, exponents (and FP64 quotients), stage in shared memory
+            // pass 1: recombine, exponents (FP64 quotients / weighted products), stage in smem
             for (int c8 = cbeg; c8 < cbeg + cols; c8 += 8) {
                 uint32_t rv[4][8], iv[4][8];
                 load_levels<S>(trow + c8, 128, rv);
@@ -436,16 +518,33 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 for (int c = 0; c < 8; ++c) {
                     const int cl = c8 + c;
                     const int qc = qbase + cl;
-                    const int eb = args.eb[qc];
+                    const int eb = colEb[cl];
                     const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                     const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                    const bool valid = row_ok && qc < n && (args.c < 2 || qc <= firstp);
+                    const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
                     unsigned key = 0;
                     if (MODE == EPI_SLICE || MODE == EPI_F64T) {
                         vbuf[((size_t)cl * NP + rl) * 2 + 0] = Vr;
                         vbuf[((size_t)cl * NP + rl) * 2 + 1] = Vi;
                         const int bl = max(bitlen64(Vr), bitlen64(Vi));
                         if (valid && bl) key = (unsigned)(bl + ea + eb - VEXP + 8192);
+                    } else if (MODE == EPI_REDUCE) {
+                        // G[c'][k] psi_{p_{N-1} k} in double-float (p_{N-1} = innermost digit)
+                        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (valid && (Vr | Vi)) {
+                            const int sc = ea + eb - VEXP;
+                            const dfl gr = df_from_i64(Vr, sc), gi = df_from_i64(Vi, sc);
+                            int pin = 0;   // innermost digit p_{N-1}, selected with static indices
+#pragma unroll
+                            for (int m = 0; m < 7; ++m)
+                                if (m == N - 2) pin = dg[m];
+                            const float4 w = args.psi_df[(int64_t)pin * n + qc];
+                            const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
+                            const dfl pr = df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi)));
+                            const dfl pi = df_add(df_mul(gr, wi), df_mul(gi, wr));
+                            g = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+                        }
+                        gbuf[(size_t)cl * NP + rl] = g;
                     } else {
                         double2 h = make_double2(0, 0);
                         if (valid && (Vr | Vi)) {
@@ -454,8 +553,16 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                                               (MODE == EPI_DIVIDE ? mult : 1.0);
                             h = make_double2((double)Vr * sc, (double)Vi * sc);
                             if (args.divide) {
-                                const double2 D = clamp_denominator(cadd(sigma, args.lam[qc]), args.eps);
-                                h = cdiv_smith(h, D);
+                                // h / D = h conj(D) / |D|^2 (FP64), D clamped per Alg. 2 step 9
+                                double2 D = cadd(sigma, args.lam[qc]);
+                                double m2 = fma(D.x, D.x, D.y * D.y);
+                                if (m2 < args.eps * args.eps) {
+                                    D = make_double2(args.eps, 0.0);
+                                    m2 = args.eps * args.eps;
+                                }
+                                const double r = __drcp_rn(m2);
+                                h = make_double2(fma(h.x, D.x, h.y * D.y) * r,
+                                                 fma(h.y, D.x, -h.x * D.y) * r);
                             }
                         }
                         hbuf[(size_t)cl * NP + rl] = h;
@@ -466,13 +573,54 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             key = (unsigned)(e + 8192);
                         }
                     }
-                    const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
-                    if (lane == 0 && wmax) atomicMax(&colE[cl], (int)wmax);
+                    if (MODE != EPI_REDUCE) {
+                        const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+                        if (lane == 0 && wmax) atomicMax(&colE[cl], (int)wmax);
+                    }
                 }
             }
         }
         asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
-        if (ok) {
+        if (trc && threadIdx.x == 64) trc[4] = global_ns();   // pass 1 done
+        if (MODE == EPI_REDUCE) {
+            // pass 2: column sums over the 128 rows (four parts per column), then the prefix
+            // weight prod_{m<=N-2} psi_{p_m k} and -sum into Psi_N[i][k]
+            const int t = (warp - 2) * 32 + lane;      // 0..255
+            const int cl = t % 64, part = t / 64;      // 4 parts of 32 rows
+            dfl sr = {0.f, 0.f}, si = {0.f, 0.f};
+            if (ok)
+                for (int r = part * 32; r < part * 32 + 32; ++r) {
+                    const float4 g = gbuf[(size_t)cl * NP + r];
+                    sr = df_add(sr, dfl{g.x, g.y});
+                    si = df_add(si, dfl{g.z, g.w});
+                }
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
+            float4* red = gbuf;                        // reuse: [4 parts][64 cols]
+            red[part * 64 + cl] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
+            const int qc = qbase + cl;
+            if (ok && part == 0 && qc < n) {
+                dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
+                for (int pp = 0; pp < 4; ++pp) {
+                    const float4 g = red[pp * 64 + cl];
+                    ar = df_add(ar, dfl{g.x, g.y});
+                    ai = df_add(ai, dfl{g.z, g.w});
+                }
+                if (ar.hi != 0.f || ai.hi != 0.f) {
+                    // the tile shares (i, p_1..p_{N-2}): recover them from the tile's first row
+                    int d0[8];
+                    row_digits((row0 % args.R), N - 1, d0);
+                    double2 w = make_double2(1.0, 0.0);
+#pragma unroll
+                    for (int m = 0; m < 6; ++m)
+                        if (m < N - 2) w = cmul(w, args.V[(int64_t)d0[m] * n + qc]);
+                    const int i = args.i0 + (int)(row0 / args.R);
+                    const double2 v = cmul(make_double2(df_to_d(ar), df_to_d(ai)), w);
+                    atomicAdd(&args.out_f64[(int64_t)i * n + qc].x, -v.x);
+                    atomicAdd(&args.out_f64[(int64_t)i * n + qc].y, -v.y);
+                }
+            }
+        } else if (ok) {
             // pass 2: outputs
             for (int cl = cbeg; cl < cbeg + cols; ++cl) {
                 const int qc = qbase + cl;
@@ -482,19 +630,20 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     if (qc < n) {
                         const long long Vr = vbuf[((size_t)cl * NP + rl) * 2 + 0];
                         const long long Vi = vbuf[((size_t)cl * NP + rl) * 2 + 1];
-                        const double sc = pow2d(ea + args.eb[qc] - VEXP);
+                        const double sc = pow2d(ea + colEb[cl] - VEXP);
                         args.out_f64[(int64_t)qc * args.ld_f64 + o] =
                             make_double2((double)Vr * sc, (double)Vi * sc);
                     }
                     continue;
                 }
                 if (MODE == EPI_SLAB) {
-                    // store h^i_{pre, q} when sort(pre + q) equals this element's tuple
+                    // store h^i_{pre, q} when the multiset (q, row p's) minus pre is {extra}
                     const double2 h = hbuf[(size_t)cl * NP + rl];
+                    const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
+                    if (!valid) continue;
                     int t[8];
                     t[0] = qc;
-                    for (int m = 0; m < np_row; ++m) t[m + 1] = dg[m];
-                    // multiset difference t \ pre must be a single index
+                    for (int m = 0; m < args.rp; ++m) t[m + 1] = dg[m];
                     int used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                     int matched = 0, extra = -1, nextra = 0;
                     for (int a = 0; a < N; ++a) {
@@ -504,12 +653,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         if (hit) ++matched;
                         else { extra = t[a]; ++nextra; }
                     }
-                    const bool valid = row_ok && qc < n && (args.c < 2 || qc <= firstp);
-                    if (valid && matched == N - 1 && nextra == 1)
+                    if (matched == N - 1 && nextra == 1)
                         args.out_f64[(int64_t)(args.i0 + outer) * n + extra] = h;
                     continue;
                 }
-                if (args.c >= 2 && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
+                if (args.colmask && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
                 const int64_t rowp = (outer * args.npc + qc) * rperq + rblk;
                 const int E = key ? key - 8192 : EXP_NONE;
                 uint32_t w[S];
@@ -517,7 +665,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 #pragma unroll
                     for (int s = 0; s < S; ++s) w[s] = 0u;
                 } else if (MODE == EPI_SLICE) {
-                    const int sh = ea + args.eb[qc] - VEXP - E + 7 + 8 * (S - 1);
+                    const int sh = ea + colEb[cl] - VEXP - E + 7 + 8 * (S - 1);
                     const long long Vr = vbuf[((size_t)cl * NP + rl) * 2 + 0];
                     const long long Vi = vbuf[((size_t)cl * NP + rl) * 2 + 1];
                     const bool valid = row_ok && qc < n;
@@ -537,6 +685,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     }
     tc::fence_before_sync();
     __syncthreads();
+    if (trc && threadIdx.x == 0) trc[5] = global_ns();
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, TMEM_COLS);
@@ -607,12 +756,14 @@ __global__ void k_expand(const uint4* __restrict__ rec, int64_t P, int n, int N,
         const int i = i0 + (int)(idx / per_i);
         int64_t f = idx % per_i;
         int a[8];
-        bool pad = false;
+        bool pad = false, unread = false;
         for (int m = N - 1; m >= 0; --m) {
             a[m] = (int)(f % NP);
             f /= NP;
             pad |= a[m] >= n;
+            if (m < N - 2) unread |= a[m] >= n;   // the contraction skips these rows' tiles
         }
+        if (unread) continue;
         uint4 r0 = make_uint4(0, 0, 0, 0), r1 = make_uint4(0, 0, 0, 0);
         if (!pad) {
             sort_small(a, N);
@@ -623,178 +774,6 @@ __global__ void k_expand(const uint4* __restrict__ rec, int64_t P, int n, int N,
         const uint32_t w[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
         for (int s = 0; s < S; ++s) planes[s * plane_stride_u32 + idx] = w[s];
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// Reduction GEMM: G^T[k][c'] = sum_{p_N} psi_{p_N k} h[c'][p_N] with Psi^T on the M side (Re
-// rows and Im rows as two MMA streams) and the h rows c' = (i, p_1..p_{N-1}) on the N side;
-// each thread (one k) folds its columns with psi_{p_{N-1} k} in double-float, multiplies by
-// prod_{m<=N-2} psi_{p_m k} and adds -sum into Psi_N[i][k].
-// ---------------------------------------------------------------------------------------
-struct RedArgs {
-    int kch;
-    const int* ea;        // [128] exponents of Psi^T rows k
-    int b_rows;           // rows per plane in the h tensor map
-    const int* eb;        // exponents of h rows c'
-    int bnc;              // columns per tile
-    int64_t num_tiles;
-    const float4* psi_df; // psi_{p k} as double-float (re.hi, re.lo, im.hi, im.lo) at p*n + k
-    const double2* V;     // psi_{p k} at p*n + k
-    int n, N, i0;
-    double2* psiN;        // [n][n], accumulated with atomics (subtracting)
-    int* err;
-};
-
-template <int S>
-struct RedCfg {
-    static constexpr int BNC = S >= 6 ? 32 : 64;   // h rows (columns of G^T) per tile
-    static constexpr int A_TILE = NP * BK * 2;      // 8 KB (128 rows)
-    static constexpr int B_TILE = BNC * BK * 2;
-    static constexpr int STAGES = S >= 4 ? 2 : 3;
-    static constexpr int STAGE_BYTES = S * (2 * A_TILE + B_TILE);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 2048;
-};
-
-template <int S>
-__global__ void __launch_bounds__(192, 1)
-    k_reduce(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             RedArgs args)
-{
-    using C = RedCfg<S>;
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
-    uint64_t* empty = full + C::STAGES;
-    uint64_t* acc_full = empty + C::STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
-
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t c0 = (int64_t)blockIdx.x * args.bnc;   // first h row of this tile
-    const int n = args.n, N = args.N;
-    // c' = (i, p_1..p_{N-1}) base NP below i; the tile shares (i, p_1..p_{N-2})
-    int dp[8];
-    row_digits(c0 % ipow_np(N - 1), N - 1, dp);
-    {
-        bool skip = false;
-        for (int m = 1; m < N - 2 + 0; ++m) skip |= dp[m - 1] > dp[m];
-        for (int m = 0; m < N - 2; ++m) skip |= dp[m] >= n;
-        if (N >= 3 && (int)(c0 % NP) + args.bnc - 1 < dp[N - 3]) skip = true;
-        if (skip) return;
-    }
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
-            tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
-        }
-        tc::mbar_init(acc_full, 1);
-        tc::fence_mbar_init();
-        tc::tma_prefetch(&tmA);
-        tc::tma_prefetch(&tmB);
-    }
-    if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, TMEM_COLS);
-        tc::tmem_relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
-    const int bnc = args.bnc;
-
-    if (warp == 0 && lane == 0) {
-        for (int kc = 0; kc < args.kch; ++kc) {
-            const int st = kc % C::STAGES;
-            const uint32_t ph = (kc / C::STAGES) & 1;
-            if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) break;
-            uint8_t* sA = smem + st * C::STAGE_BYTES;
-            uint8_t* sB = sA + 2 * S * C::A_TILE;
-            tc::mbar_arrive_expect_tx(&full[st], S * (2 * C::A_TILE + bnc * BK * 2));
-            for (int s = 0; s < S; ++s) {
-                tc::tma_load_2d(sA + (2 * s) * C::A_TILE, &tmA, kc * BK, s * 512, &full[st]);
-                tc::tma_load_2d(sA + (2 * s + 1) * C::A_TILE, &tmA, kc * BK, s * 512 + 256,
-                                &full[st]);
-                tc::tma_load_2d(sB + s * C::B_TILE, &tmB, kc * BK, s * args.b_rows + (int)c0,
-                                &full[st]);
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        const uint32_t idesc = tc::idesc_bf16_f32(128, bnc);
-        bool first[4] = {true, true, true, true};
-        for (int kc = 0; kc < args.kch; ++kc) {
-            const int st = kc % C::STAGES;
-            const uint32_t ph = (kc / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) break;
-            tc::fence_after_sync();
-            const uint32_t aBase = tc::smem_u32(smem + st * C::STAGE_BYTES);
-            const uint32_t bBase = aBase + 2 * S * C::A_TILE;
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-#pragma unroll
-                for (int t = 0; t < S - s; ++t) {
-                    const int L = s + t < 3 ? s + t : 3;
-#pragma unroll
-                    for (int ks = 0; ks < BK / 16; ++ks) {
-                        const uint64_t bd = tc::sdesc_sw64(bBase + t * C::B_TILE + ks * 32);
-                        const uint64_t adr = tc::sdesc_sw64(aBase + (2 * s) * C::A_TILE + ks * 32);
-                        const uint64_t adi =
-                            tc::sdesc_sw64(aBase + (2 * s + 1) * C::A_TILE + ks * 32);
-                        const uint32_t acc = first[L] ? 0u : 1u;
-                        tc::mma_bf16(tmem + L * C::BNC, adr, bd, idesc, acc);
-                        tc::mma_bf16(tmem + 256 + L * C::BNC, adi, bd, idesc, acc);
-                        first[L] = false;
-                    }
-                }
-            tc::mma_commit(&empty[st]);
-        }
-        tc::mma_commit(acc_full);
-    } else if (warp >= 2) {
-        const int q4 = warp % 4;
-        const int k = q4 * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
-        const bool ok = tc::mbar_wait(acc_full, 0, args.err, kErrTimeout);
-        tc::fence_after_sync();
-        if (ok) {
-            const int ea = k < n ? args.ea[k] : 0;
-            const int lowp = N >= 3 ? dp[N - 3] : 0;   // p_{N-2} (columns need p_{N-1} >= it)
-            dfl sr = {0.f, 0.f}, si = {0.f, 0.f};
-            for (int c8 = 0; c8 < bnc; c8 += 8) {
-                uint32_t rv[4][8], iv[4][8];
-                load_levels<S>(trow + c8, C::BNC, rv);
-                load_levels<S>(trow + 256 + c8, C::BNC, iv);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int64_t col = c0 + c8 + c;
-                    const int p = (int)(col % NP);           // p_{N-1}
-                    if (k >= n || p >= n || p < lowp) continue;
-                    const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
-                    const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                    if (!(Vr | Vi)) continue;
-                    const int sc = ea + args.eb[col] - VEXP;
-                    const dfl gr = df_from_i64(Vr, sc), gi = df_from_i64(Vi, sc);
-                    const float4 w = args.psi_df[(int64_t)p * n + k];
-                    const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
-                    sr = df_add(sr, df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi))));
-                    si = df_add(si, df_add(df_mul(gr, wi), df_mul(gi, wr)));
-                }
-            }
-            if (k < n && (sr.hi != 0.f || si.hi != 0.f)) {
-                double2 w = make_double2(1.0, 0.0);
-                for (int m = 0; m < N - 2; ++m) w = cmul(w, args.V[(int64_t)dp[m] * n + k]);
-                const int i = args.i0 + (int)(c0 / ipow_np(N - 1));
-                const double2 t = cmul(make_double2(df_to_d(sr), df_to_d(si)), w);
-                atomicAdd(&args.psiN[(int64_t)i * n + k].x, -t.x);
-                atomicAdd(&args.psiN[(int64_t)i * n + k].y, -t.y);
-            }
-        }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 1) {
-        tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, TMEM_COLS);
     }
 }
 
@@ -948,7 +927,7 @@ static void set_smem_attrs()
     NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_SLICE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
     NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_DIVIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
     NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_SLAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_reduce<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RedCfg<S>::SMEM));
+    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
     done = true;
 }
 
@@ -1028,13 +1007,58 @@ void split_prepare_tensor(Plan& p, int N)
     }
 }
 
+// Tracing aid: with NPF_TRACE_TILES set in the environment every k_rows launch records per-CTA
+// phase times (%globaltimer) and prints the median phase durations to stderr.
+static void trace_report(const char* name, const std::vector<unsigned long long>& t, int64_t tiles)
+{
+    std::vector<double> d[5];
+    unsigned long long t0 = ~0ull, t1 = 0;
+    int64_t ran = 0;
+    for (int64_t k = 0; k < tiles; ++k) {
+        const unsigned long long* r = &t[k * 6];
+        if (!r[0] || !r[5]) continue;
+        ++ran;
+        t0 = std::min(t0, r[0]);
+        t1 = std::max(t1, r[5]);
+        d[0].push_back((double)(r[1] - r[0]));   // setup (barriers, TMEM alloc)
+        d[1].push_back((double)(r[2] - r[1]));   // first stage fill
+        d[2].push_back((double)(r[3] - r[2]));   // MMA from first stage to completion
+        d[3].push_back((double)(r[4] - r[3]));   // epilogue pass 1
+        d[4].push_back((double)(r[5] - r[4]));   // epilogue pass 2 + teardown
+    }
+    auto med = [](std::vector<double>& v) {
+        if (v.empty()) return 0.0;
+        std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+        return v[v.size() / 2] * 1e-3;
+    };
+    fprintf(stderr, "[trace] %s tiles %lld ran %lld span %.1f us | median us: setup %.2f fill %.2f "
+            "mma %.2f epi1 %.2f epi2 %.2f\n", name, (long long)tiles, (long long)ran,
+            (t1 > t0 ? (t1 - t0) : 0) * 1e-3, med(d[0]), med(d[1]), med(d[2]), med(d[3]), med(d[4]));
+}
+
 template <int S, int MODE>
 static void launch_rows(Plan& p, const char* name, const CUtensorMap& tA, const CUtensorMap& tB,
-                        const RowArgs& a)
+                        RowArgs a)
 {
-    LaunchScope ls(&p.prof, name, p.stream);
-    k_rows<S, MODE><<<(unsigned)a.num_tiles, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
-    NPF_CUDA(cudaGetLastError());
+    static const bool tracing = getenv("NPF_TRACE_TILES") != nullptr;
+    unsigned long long* dtrace = nullptr;
+    if (tracing) {
+        NPF_CUDA(cudaMalloc(&dtrace, (size_t)a.num_tiles * 6 * 8));
+        NPF_CUDA(cudaMemsetAsync(dtrace, 0, (size_t)a.num_tiles * 6 * 8, p.stream));
+        a.trace = dtrace;
+    }
+    {
+        LaunchScope ls(&p.prof, name, p.stream);
+        k_rows<S, MODE><<<(unsigned)a.num_tiles, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+        NPF_CUDA(cudaGetLastError());
+    }
+    if (tracing) {
+        std::vector<unsigned long long> h((size_t)a.num_tiles * 6);
+        NPF_CUDA(cudaMemcpyAsync(h.data(), dtrace, h.size() * 8, cudaMemcpyDeviceToHost, p.stream));
+        NPF_CUDA(cudaStreamSynchronize(p.stream));
+        cudaFree(dtrace);
+        trace_report(name, h, a.num_tiles);
+    }
 }
 
 static double factorial(int N) { double f = 1; for (int t = 2; t <= N; ++t) f *= t; return f; }
@@ -1076,27 +1100,26 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
 
     if (!slab) launch_zero(p, d_out, (int64_t)n * n);
 
-    const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, 64);
-    const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, 64);
-    const CUtensorMap tRed = make_tmap(so.red, KP, (int64_t)S * 512, 128);
+    const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, p.tile_n);
+    const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, p.tile_n);
+    const CUtensorMap tRed = make_tmap(so.red, KP, (int64_t)S * 512, p.tile_n);
     const CUtensorMap tAT = make_tmap(so.at[N], NP, (int64_t)S * Prows, 128);
     const CUtensorMap tT0 = make_tmap(T[0], KP, (int64_t)S * t_rows, 128);
     const CUtensorMap tT1 = make_tmap(T[1], KP, (int64_t)S * t_rows, 128);
-    const CUtensorMap tTB0 = make_tmap(T[0], KP, (int64_t)S * t_rows, RedCfg<S>::BNC);
-    const CUtensorMap tTB1 = make_tmap(T[1], KP, (int64_t)S * t_rows, RedCfg<S>::BNC);
     const CUtensorMap* tT[2] = {&tT0, &tT1};
-    const CUtensorMap* tTB[2] = {&tTB0, &tTB1};
 
     RowArgs base0{};
     base0.n = n;
     base0.N = N;
+    base0.V = p.d_V;
+    base0.psi_df = so.psi_df;
     base0.lam = p.d_lam;
     base0.invfact = 1.0 / factorial(N);
     base0.eps = p.eps;
     base0.divide = p.divide;
     base0.err = so.err;
-    base0.bnc = 64;
-    base0.ncol_tiles = 2;
+    base0.bnc = p.tile_n;
+    base0.ncol_tiles = NP / p.tile_n;
     if (slab)
         for (int m = 0; m < N - 1; ++m) base0.pre[m] = prefix[m];
 
@@ -1108,8 +1131,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
         a.ea = so.at_e[N];
         a.ea_shift = 0;
         a.eb = so.psir_e;
-        a.num_tiles = Prows / NP * 2;
-        a.c = 0;
+        a.num_tiles = Prows / NP * a.ncol_tiles;
+        a.digits = 0;
         a.R = Prows;
         a.npc = n;
         a.out_f64 = Sd;
@@ -1140,8 +1163,10 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
             a.ea = c == 1 ? sE + i0 : E[cb];
             a.ea_shift = c == 1 ? 7 * (N - 1) : 0;
             a.eb = so.phi_e;
-            a.num_tiles = rows / NP * 2;
-            a.c = c;
+            a.num_tiles = rows / NP * a.ncol_tiles;
+            a.digits = 1;
+            a.rp = c - 1;              // p_{N-c+2}..p_N lead the row, then a_1..a_{N-c}
+            a.colmask = c >= 2;        // new index p_{N-c+1} <= p_{N-c+2}
             a.R = npN1;
             a.npc = NP;
             a.i0 = i0;
@@ -1159,23 +1184,22 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
             cb ^= 1;
         }
         if (slab) continue;
-        RedArgs r{};
-        r.kch = KP / BK;
-        r.ea = so.red_e;
-        r.b_rows = (int)t_rows;
-        r.eb = E[cb];
-        r.bnc = RedCfg<S>::BNC;
-        r.num_tiles = rows / RedCfg<S>::BNC;
-        r.psi_df = so.psi_df;
-        r.V = p.d_V;
-        r.n = n;
-        r.N = N;
-        r.i0 = i0;
-        r.psiN = d_out;
-        r.err = so.err;
-        LaunchScope ls(&p.prof, "split_reduce", p.stream);
-        k_reduce<S><<<(unsigned)r.num_tiles, 192, RedCfg<S>::SMEM, p.stream>>>(tRed, *tTB[cb], r);
-        NPF_CUDA(cudaGetLastError());
+        // ---- reduction: rows c' = (i, p_1..p_{N-1}), K = p_N, columns k (Psi^T)
+        RowArgs a = base0;
+        a.a_rows = (int)t_rows;
+        a.kch = KP / BK;
+        a.ea = E[cb];
+        a.ea_shift = 0;
+        a.eb = so.red_e;
+        a.num_tiles = rows / NP * a.ncol_tiles;
+        a.digits = 1;
+        a.rp = N - 1;
+        a.colmask = 0;
+        a.R = npN1;
+        a.npc = NP;
+        a.i0 = i0;
+        a.out_f64 = d_out;
+        launch_rows<S, EPI_REDUCE>(p, "split_reduce", *tT[cb], tRed, a);
     }
     int herr = 0;
     NPF_CUDA(cudaMemcpyAsync(&herr, so.err, sizeof(int), cudaMemcpyDeviceToHost, p.stream));

@@ -276,6 +276,12 @@ int npf_set_option(npf_handle* h, int key, double value)
         case NPF_OPT_PROFILE:
             p.prof.enabled = value != 0.0;
             break;
+        case NPF_OPT_TILE_N: {
+            const int v = (int)value;
+            if (v != 16 && v != 32 && v != 64) npf::fail(NPF_ERR_ARG, "tile width must be 16, 32 or 64");
+            p.tile_n = v;
+            break;
+        }
         default:
             npf::fail(NPF_ERR_ARG, "unknown option key");
         }
