@@ -142,6 +142,23 @@ int npf_get_profile(npf_handle* h, int cap, const char** names, int64_t* launche
 /* Number of kernels this library has launched in the process so far (all handles). */
 int64_t npf_launch_count(void);
 
+/* The order-`order` term Psi_N[i*n + k] computed by the native-FP64 kernels without allocating
+ * any device memory (the paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc -- code running while a CUDA graph it does not own is being captured, processes held
+ * to a memory pool they were given, plugins whose host application forbids device allocations).
+ * Every pointer is a DEVICE pointer owned by the caller: eigvals[n], U[n*n], V[n*n] (layouts as
+ * for npf_plan), coeffs = the packed order-`order` tensor, out[n*n]. eps is the clamp of
+ * Algorithm 2 step 9. stream is a cudaStream_t (NULL = legacy default); the call returns after
+ * the stream has finished. Scratch is one file-scope device array of 64 MiB per device (kept
+ * until the process exits); a problem whose scratch does not fit (all of 2 n^N + n^(N-1) complex
+ * values for one output-index batch, plus small tables) is rejected with NPF_ERR_UNSUPPORTED
+ * before any work. The first call on a device looks up the array's device address (set-up, once
+ * per device): make it before any stream capture. All calls share the array, so calls that
+ * overlap on the GPU race on it. */
+int npf_term_fp64_noalloc(int n, int order, const npf_c128* eigvals, const npf_c128* U,
+                          const npf_c128* V, const double* coeffs, double eps, npf_c128* out,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 //   4. Psi_N[i,k] -= sum_p h^i_p prod_m psi_{p_m k} (steps 12-19): one GEMM with Psi over pb,
 //      then N-1 "diagonal" contractions with psi_{p_m k}.
 #include <algorithm>
+#include <mutex>
 
 #include "k_device.cuh"
 #include "npf_internal.h"
@@ -295,4 +296,166 @@ void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out)
     gemm(p, "fp64_psi_divide", X, n, n, p.d_Vt, n, n, d_out, 2, da);
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the order-N term, for callers that cannot call cudaMalloc: code
+// that runs while a CUDA graph it does not own is being captured, processes that must stay
+// inside a memory pool handed to them, or plugins whose host application forbids device
+// allocations. Its scratch is the file-scope array below, NOALLOC_SCRATCH_BYTES per device,
+// which every device that loads this library keeps until the process exits. Host code must not
+// pass `g_noalloc_scratch` itself to a kernel (on the host that name is only a stand-in); the
+// device address comes from cudaGetSymbolAddress, looked up once per device by the first call
+// made with that device current -- make that first call before any stream capture.
+// Every call shares the one array: calls that overlap on the GPU (other streams, other host
+// threads) race on it.
+// ---------------------------------------------------------------------------------------
+constexpr size_t NOALLOC_SCRATCH_BYTES = 64ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// cnt[r*(n+1) + v] = C(n - v + r - 1, r): non-decreasing r-tuples with values in [v, n)
+__global__ void k_noalloc_cnt(int n, int R, int64_t* __restrict__ cnt)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * (n + 1)) return;
+    const int r = idx / (n + 1), v = idx % (n + 1);
+    const int64_t m = n - v;
+    int64_t c;
+    if (r == 0) c = 1;
+    else if (m == 0) c = 0;
+    else { c = 1; for (int t = 1; t <= r; ++t) c = c * (m - 1 + t) / t; }
+    cnt[idx] = c;
+}
+
+// Vt[k*n + i] = V[i*n + k]
+__global__ void k_noalloc_transpose(int n, const double2* __restrict__ V, double2* __restrict__ Vt)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int i = idx / n, k = idx % n;
+    Vt[(int64_t)k * n + i] = V[idx];
+}
+
+static void* noalloc_scratch_address()
+{
+    static std::mutex mu;
+    static void* addr[64] = {};
+    int dev = 0;
+    NPF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(NPF_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            fail(NPF_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") +
+                                   cudaGetErrorString(e));
+        addr[dev] = ptr;
+    }
+    return addr[dev];
+}
+
+static void fp64_term_noalloc(int n, int N, const double2* lam, const double2* U, const double2* V,
+                              const double* A, double eps, double2* d_out, cudaStream_t s)
+{
+    if (n < 1 || n > kMaxN) fail(NPF_ERR_ARG, "n must be in [1, 4096]");
+    if (N < 2 || N > kMaxOrder) fail(NPF_ERR_ARG, "order must be in [2, 6]");
+    if (!lam || !U || !V || !A || !d_out) fail(NPF_ERR_ARG, "null pointer");
+    if (!(eps > 0.0)) fail(NPF_ERR_ARG, "eps must be > 0");
+    const int64_t nN = ipow64(n, N);
+    const size_t cnt_bytes = ((size_t)(N + 1) * (n + 1) * sizeof(int64_t) + 255) & ~(size_t)255;
+    const size_t vt_bytes = ((size_t)n * n * sizeof(double2) + 255) & ~(size_t)255;
+    const size_t per_nb = (2 * (size_t)nN + (size_t)nN / n) * sizeof(double2);
+    const size_t fixed = cnt_bytes + vt_bytes;
+    if (fixed + per_nb > NOALLOC_SCRATCH_BYTES)
+        fail(NPF_ERR_UNSUPPORTED,
+             "n = " + std::to_string(n) + ", order " + std::to_string(N) + " needs " +
+                 std::to_string((fixed + per_nb) >> 20) + " MiB of scratch; the allocation-free "
+                 "entry point holds 64 MiB (use npf_plan/npf_get_term instead)");
+    uint8_t* base = (uint8_t*)noalloc_scratch_address();
+    const int nb = (int)std::min<size_t>((size_t)n, (NOALLOC_SCRATCH_BYTES - fixed) / per_nb);
+
+    Plan tmp;   // describes the caller's buffers; owns nothing
+    tmp.n = n;
+    tmp.Nmax = N;
+    tmp.stream = s;
+    tmp.eps = eps;
+    tmp.divide = 1;
+    tmp.d_lam = const_cast<double2*>(lam);
+    tmp.d_U = const_cast<double2*>(U);
+    tmp.d_V = const_cast<double2*>(V);
+    tmp.d_cnt = (int64_t*)base;
+    tmp.d_Vt = (double2*)(base + cnt_bytes);
+    tmp.d_tensor[N] = const_cast<double*>(A);
+    tmp.packed_count[N] = packed_count(n, N);
+    double2* bufA = (double2*)(base + fixed);
+    double2* bufB = bufA + (size_t)nb * nN;
+    double2* bufC = bufB + (size_t)nb * nN;
+    {
+        LaunchScope ls(nullptr, "noalloc_tables", s);
+        k_noalloc_cnt<<<((N + 1) * (n + 1) + 255) / 256, 256, 0, s>>>(n, N + 1, tmp.d_cnt);
+        k_noalloc_transpose<<<(n * n + 255) / 256, 256, 0, s>>>(n, V, tmp.d_Vt);
+        NPF_CUDA(cudaGetLastError());
+    }
+    launch_zero(tmp, d_out, (int64_t)n * n);
+    DivideArgs none = divide_args(tmp, N);
+    const int64_t nT = ipow64(n, N - 1);
+    for (int b0 = 0; b0 < n; b0 += nb) {
+        const int cur = std::min(nb, n - b0);
+        {
+            LaunchScope ls(nullptr, "fp64_first_contraction", s);
+            const int64_t tot = (int64_t)n * nT;
+            k64_first<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(
+                n, N, A, tmp.packed_count[N], tmp.d_cnt, U, b0, cur, bufA);
+            NPF_CUDA(cudaGetLastError());
+        }
+        const int64_t total = (int64_t)cur * nN;
+        double2* X = bufA;
+        double2* Y = bufB;
+        for (int m = 2; m <= N; ++m) {
+            gemm(tmp, "fp64_mode_product", X, total / n, n, U, n, n, Y, 0, none);
+            std::swap(X, Y);
+        }
+        DivideArgs da = divide_args(tmp, N);
+        da.ndig = N - 1;
+        da.nlast = cur;
+        da.off_last = b0;
+        gemm(tmp, "fp64_psi_divide", X, total / n, n, tmp.d_Vt, n, n, Y, 2, da);
+        std::swap(X, Y);
+        const int64_t nN1 = nN / n;
+        for (int i0 = 0; i0 < n; i0 += nb) {
+            const int c = std::min(nb, n - i0);
+            gemm(tmp, "fp64_reduce_gemm", X + (int64_t)i0 * nN1 * cur, (int64_t)c * nN1, cur,
+                 V + (int64_t)b0 * n, n, n, Y, 1, none);
+            double2* src = Y;
+            double2* dst = bufC;
+            int64_t O = (int64_t)c * nN1 / n;
+            for (int m = N - 1; m >= 1; --m) {
+                LaunchScope ls(nullptr, "fp64_khatri_rao_diag", s);
+                const bool last = (m == 1);
+                const int64_t cnt = O * n;
+                k64_diag<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+                    n, O, n, 0, src, V, last ? d_out + (int64_t)i0 * n : dst, last ? 1 : 0);
+                NPF_CUDA(cudaGetLastError());
+                if (!last) { std::swap(src, dst); O /= n; }
+            }
+        }
+    }
+    NPF_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace npf
+
+// Allocation-free order-N term (declared in include/npf.h).
+extern "C" int npf_term_fp64_noalloc(int n, int order, const npf_c128* eigvals, const npf_c128* U,
+                                     const npf_c128* V, const double* coeffs, double eps,
+                                     npf_c128* out, void* stream)
+{
+    try {
+        npf::fp64_term_noalloc(n, order, (const double2*)eigvals, (const double2*)U,
+                               (const double2*)V, coeffs, eps, (double2*)out, (cudaStream_t)stream);
+        return npf::record_status(NPF_OK, "");
+    } catch (const npf::Error& e) {
+        return npf::record_status(e.code, e.msg);
+    } catch (...) {
+        return npf::record_status(NPF_ERR_CUDA, "unknown error");
+    }
+}

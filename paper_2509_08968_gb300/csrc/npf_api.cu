@@ -92,6 +92,18 @@ void compute_npf(Plan& p, int order)
 
 }  // namespace
 
+namespace npf {
+// Record a status for npf_last_error()/npf_last_status() from another translation unit.
+int record_status(int code, const std::string& msg)
+{
+    if (code == NPF_OK) {
+        g_status = NPF_OK;
+        return NPF_OK;
+    }
+    return set_error(code, msg);
+}
+}  // namespace npf
+
 extern "C" {
 
 const char* npf_last_error(void) { return g_err.c_str(); }

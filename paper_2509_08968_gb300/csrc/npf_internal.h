@@ -24,6 +24,7 @@ struct Error {
     std::string msg;
 };
 [[noreturn]] void fail(int code, const std::string& msg);
+int record_status(int code, const std::string& msg);   // thread-local status of the C ABI
 void check_cuda(cudaError_t e, const char* what);
 #define NPF_CUDA(x) ::npf::check_cuda((x), #x)
 
