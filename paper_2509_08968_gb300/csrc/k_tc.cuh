@@ -45,14 +45,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity to complete; gives up after kWaitLimit polls,
-// records `code` in *err and returns false.
+// Wait for the phase with the given parity to complete; gives up after kWaitLimit polls (or as
+// soon as another role of the kernel has recorded an error), records `code` in *err and returns
+// false.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code)
 {
-    for (long long it = 0; it < kWaitLimit; ++it)
+    for (long long it = 0; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 1023) == 1023 && *(volatile int*)err) return false;
+    }
     atomicCAS(err, 0, code);
     return false;
+}
+
+// Arrive once on `bar` (plain arrive, no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // ---------------------------------------------------------------------------- TMA
