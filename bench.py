@@ -29,7 +29,8 @@ sys.path.insert(0, ROOT)
 N_STATES = 120
 ORDERS = (3, 4)
 # name -> (n, orders)
-WORKLOADS = {"n120": (120, (3, 4)), "n60": (60, (3, 4)), "n120o3": (120, (3,))}
+WORKLOADS = {"n120": (120, (3, 4)), "n60": (60, (3, 4)), "n120o3": (120, (3,)),
+             "batch256": (None, (2, 3)), "surrogate": (40, (2, 3))}
 METRIC = "modal-tensor entries/s & % roofline, split-prec vs native FP64 at rel err <=1e-10"
 
 
@@ -93,6 +94,21 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def aggregate(dist, t, units):
+    """Whole-job view of one rank's step: (max of t over ranks, sum of units over ranks). Every
+    rank works on its own problem (weak scaling), so this pair is the only exchange; on NCCL the
+    values travel on the GPU, on gloo on the host."""
+    if dist is None:
+        return t, units
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tm = torch.tensor([float(t)], dtype=torch.float64, device=dev)
+    us = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(us, op=dist.ReduceOp.SUM)
+    return float(tm.item()), float(us.item())
 
 
 def dist_setup():
@@ -179,6 +195,10 @@ def main():
     import paper_2509_08968_gb300 as npf
     from paper_2509_08968_gb300 import build
     build.build()
+    if args.workload == "batch256":
+        return run_batch(args, world, rank, local, dist)
+    if args.workload == "surrogate":
+        return run_surrogate(args, world, rank, local, dist)
 
     global N_STATES, ORDERS
     N_STATES, ORDERS = WORKLOADS[args.workload]
@@ -224,11 +244,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     prof = plan.profile(reset=True)
     plan.set_option(npf.OPT_PROFILE, 0)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ents = entries_per_step(n) * world
+    ms, ents = aggregate(dist, ms, entries_per_step(n))
     value = ents / (ms * 1e-3)
 
     # ---- roofline of the dominant kernel (live CUDA-event durations of the timed steps)
@@ -275,8 +291,8 @@ def main():
         for _ in range(steps_e2e):
             e2e_step()
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / steps_e2e
-        e2e = {"value": entries_per_step(n) * world / dt, "unit": "entries/s",
+        dt, e_all = aggregate(dist, (time.perf_counter() - t0) / steps_e2e, entries_per_step(n))
+        e2e = {"value": e_all / dt, "unit": "entries/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
 
     cpu = None
@@ -288,8 +304,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"split_bf16": "bf16x5-split (fp64-emulating)", "fp32": "bf16x3-split",
-                      "fp64": "f64"}[args.precision],
+            "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": f"n={n} block-structured system ({n // 4} blocks x 4 states), "
                                    f"NPF orders {', '.join(map(str, ORDERS))}, packed symmetric "
@@ -307,6 +322,211 @@ def main():
     return 0
 
 
+def run_batch(args, world, rank, local, dist):
+    """256 independent systems, n ~ U{20..80} (even), orders drawn from {2, 3}, about 5% of the
+    ordered mode pairs within 1e-3 of a resonance; one npf_batch_compute per step (one recorded
+    CUDA graph, tile widths autotuned). Metric: sum over systems of n^(N+1) per second."""
+    import torch
+    import npf_synth as S
+    import paper_2509_08968_gb300 as npf
+    systems = S.batch_systems(count=256, seed=rank)
+    plans, orders, outs = [], [], []
+    for sysm, N in systems:
+        p = npf.Plan(sysm.lam, sysm.U, sysm.V, N, precision=args.precision)
+        p.set_option(npf.OPT_TILE_N, args.tile_n)   # 0 = autotuned
+        p.set_tensor(N, torch.from_numpy(sysm.tensors[N]).cuda())
+        plans.append(p)
+        orders.append(N)
+        outs.append(torch.empty((sysm.n, sysm.n), dtype=torch.complex128, device="cuda"))
+    ents = sum(s.n ** (N + 1) for s, N in systems)
+
+    def step():
+        npf.batch_compute(plans, orders, outs)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = npf.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()          # returns after its graph and copies have finished
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = npf.launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms, ents_all = aggregate(dist, ms, ents)
+    value = ents_all / (ms * 1e-3)
+
+    # whole-step tensor roofline: algorithmic (sorted-tuple, unpadded) BF16 flops of every system
+    from math import comb
+    pairs = PAIRS[args.precision]
+    useful = executed = 0.0
+    tiles = {}
+    for s, N in systems:
+        n = s.n
+        f = n * comb(n + N - 1, N) * n * 4
+        f += sum(n * comb(n + c - 1, c) * n ** (N - c) * n * 8 for c in range(1, N))
+        f += n * comb(n + N - 1, N) * n * 8 + n * comb(n + N - 2, N - 1) * n * n * 8
+        f *= pairs
+        t = args.tile_n or npf.tuned_tile(n, N, args.precision) or 64
+        tiles[f"n{n}o{N}"] = t
+        # padded tile shape: 128 rows per innermost row index, K' in chunks of 32, t columns
+        r = (128 / n) * (32 * -(-2 * n // 32) / (2 * n)) * (t * -(-n // t) / n)
+        useful += f
+        executed += f * r
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = useful / (ms * 1e-3) / 1e12
+    roof = None
+    if args.precision != "fp64":
+        roof = {"kernel": "whole step (all systems)", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"bf16 sustained ({src})"}
+
+    e2e = None
+    if not args.no_e2e:
+        host_t = [torch.from_numpy(s.tensors[N]).pin_memory() for s, N in systems]
+        host_o = [torch.empty((s.n, s.n), dtype=torch.complex128).pin_memory() for s, _ in systems]
+        h2d = sum(int(t.numel() * 8) for t in host_t)
+        d2h = sum(int(o.numel() * 16) for o in host_o)
+
+        def e2e_step():
+            for p, N, t in zip(plans, orders, host_t):
+                p.set_tensor(N, t)
+            npf.batch_compute(plans, orders, host_o)
+
+        e2e_step()
+        steps_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            e2e_step()
+        dt, e_all = aggregate(dist, (time.perf_counter() - t0) / steps_e2e, ents)
+        e2e = {"value": e_all / dt, "unit": "entries/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
+    if rank == 0:
+        ns = [s.n for s, _ in systems]
+        line = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": "256 systems, n ~ U{20..80} (even), orders U{2,3}, ~5% of mode "
+                                   "pairs within 1e-3 of resonance, one recorded graph per step",
+                       "systems": len(systems), "n_min": min(ns), "n_max": max(ns),
+                       "entries_per_step": ents, "precision": args.precision,
+                       "padding_fraction_est": 1.0 - useful / executed if executed else None,
+                       "tiles": tiles,
+                       "l2": "inputs larger than L2 (packed tensors and scratch ~GBs)"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line))
+    for p in plans:
+        p.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_surrogate(args, world, rank, local, dist):
+    """Learned surrogate over a family of operating points (n = 40, orders 2 and 3): 4096
+    training labels and 512 held-out labels from the plain method, an ensemble of five BF16 MLPs
+    4 -> 256 -> 256 -> 256 -> 64 trained by the library, then one step = gated prediction of the
+    512 held-out points (members' spread > 5% -> plain method). Metric: queries per second."""
+    import torch
+    import npf_synth as S
+    from paper_2509_08968_gb300 import surrogate as SG
+    fam = S.surrogate_family(40, rank)
+    lam_ref = np.linalg.eigvals(fam.A(fam.p0))
+    solver = SG.PlainSolver(fam, 3, lam_ref, slots=256, precision=args.precision)
+    idx = SG.top_indices(solver.npf(fam.p0[None])[0], 64)
+    solver.indices = idx
+    Ptr = S.operating_points(fam, 4096, 2 * rank)
+    Pte = S.operating_points(fam, 512, 2 * rank + 1)
+    t0 = time.perf_counter()
+    Ytr = solver.values(Ptr)
+    t_label = time.perf_counter() - t0
+    solver.values(Pte)                       # records the 256-system graph for this pool
+    t0 = time.perf_counter()
+    Yte = solver.values(Pte)
+    t_plain = time.perf_counter() - t0
+    sur = SG.Surrogate(fam, idx, [4, 256, 256, 256, 64], ensemble=5, seed=0)
+    t0 = time.perf_counter()
+    hist = sur.fit(Ptr, Ytr, epochs=300, batch=256, lr=1e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    for _ in range(max(3, args.warmup)):
+        sur.gated(Pte, solver, 0.05)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    from paper_2509_08968_gb300 import launch_count
+    l0 = launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out, spread, fb = sur.gated(Pte, solver, 0.05)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    launches = launch_count() - l0
+    clk = clocks.stop()
+    dt, q_all = aggregate(dist, dt, len(Pte))
+    mean, _, _ = sur.predict(Pte, 0.05)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sur.predict(Pte, 0.05)
+    t_sur = (time.perf_counter() - t0) / args.steps
+    rel = np.abs(out - Yte) / Yte
+    rel_ungated = np.abs(mean - Yte) / Yte
+    if rank == 0:
+        line = {
+            "metric": "surrogate queries/s (gated at 5% ensemble spread, plain-method fallback)",
+            "value": q_all / dt, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (MLP), " + DTYPES[args.precision]
+            + " (fallback)", "data": "synthetic",
+            "config": {"workload": "operating-point family n=40, NPF order 3 (A2, A3), p = (load "
+                                   "scale U[0.6,1.2], 3 gains U[0.5,2]), top-64 |NPF|, 4096 train "
+                                   "+ 512 held-out, ensemble 5 x MLP 4-256-256-256-64",
+                       "l2": "small working set (latency-bound MLP), no L2 flush"},
+            "surrogate": {"plain_queries_per_s": len(Pte) / t_plain,
+                          "ungated_queries_per_s": len(Pte) / t_sur,
+                          "speedup_gated_vs_plain": t_plain / dt,
+                          "fallback_rate": float(fb.mean()),
+                          "heldout_rel_err_gated": {"median": float(np.median(rel)),
+                                                    "p95": float(np.percentile(rel, 95)),
+                                                    "max": float(rel.max())},
+                          "heldout_rel_err_ungated": {"median": float(np.median(rel_ungated)),
+                                                      "p95": float(np.percentile(rel_ungated, 95)),
+                                                      "max": float(rel_ungated.max())},
+                          "train_s": t_train, "train_loss_first_last": [float(hist[0]),
+                                                                        float(hist[-1])],
+                          "label_queries_per_s": len(Ptr) / t_label},
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": q_all / dt, "unit": "queries/s", "h2d_bytes_per_step": 512 * 4 * 4,
+                    "d2h_bytes_per_step": 512 * (64 * 4 + 8)},
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line))
+    sur.close()
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+DTYPES = {"split_bf16": "bf16x6-split (fp64-emulating)", "fp32": "bf16x3-split", "fp64": "f64"}
 PAIRS = {"split_bf16": 21, "fp32": 6, "fp64": 1}     # BF16 slice pairs s + t < S (S = 6 / 3)
 SLICES = {"split_bf16": 6, "fp32": 3, "fp64": 0}
 

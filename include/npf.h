@@ -74,7 +74,10 @@ enum npf_option {
                                sum_p C^i_p prod_m psi_{p_m k} = (1/N!) sum_j psi_ij A^j_{k..k}. */
     NPF_OPT_MEM_BUDGET = 5, /* bytes of device memory for intermediates; 0 = 80% of free memory. */
     NPF_OPT_PROFILE = 6,    /* 1: time each kernel launch with CUDA events (npf_get_profile). */
-    NPF_OPT_TILE_N = 7      /* complex columns per tensor-core tile: 16, 32 or 64 (default 64). */
+    NPF_OPT_TILE_N = 7      /* complex columns per tensor-core tile: 16, 32 or 64 (default 64), or
+                               0 = autotuned: the first term of each (n, order, precision,
+                               slices, divide) times every width on the plan's own work and the
+                               fastest is kept for the process (npf_tuned_tile). */
 };
 
 /* Arithmetic of the dense contraction. The denominators, the divide, the Psi_N sums and the
@@ -93,6 +96,12 @@ enum npf_precision {
  * Returns NULL on error (npf_last_error() tells why; npf_last_status() gives the code). */
 npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* U,
                      const npf_c128* V, size_t mem_budget);
+
+/* Replace the modal data of a plan by another system of the same size (eigvals[n], U, V as for
+ * npf_plan, same check). Tensors, options and device buffers are kept, so a recorded batch
+ * graph (npf_batch_compute) that holds this plan stays valid and computes the new system. Not in
+ * the paper: for sweeps over operating points of one model. */
+int npf_set_modes(npf_handle* h, const npf_c128* eigvals, const npf_c128* U, const npf_c128* V);
 
 /* Copy the packed order-`order` tensor (2 <= order <= N_max; layout above; host or device) into
  * the plan's device memory. Replaces a previous tensor of that order. */
@@ -116,11 +125,24 @@ int npf_get_term(npf_handle* h, int order, npf_c128* out);
  * [0, n)), every mode i and last index q. Host or device `out`. For parity checks at full size. */
 int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* out);
 
-/* Many plans in one call (independent systems of uneven size and order): computes
- * NPF_{orders[b]} of plans[b] into outs[b] for b < count. Work of all systems is issued as one
- * captured CUDA graph on the first plan's stream. */
+/* Many plans in one call (independent systems of uneven size and order; the paper notes that its
+ * batches are independent, Section II.B): computes NPF_{orders[b]} of plans[b] into outs[b]
+ * (host or device, n_b*n_b each) for b < count. Each plan appears at most once. The systems are
+ * spread over library-owned streams (longest work first onto the least-loaded stream). The first
+ * call for a given list of (plan, order) runs the work eagerly on those streams (tile tuning,
+ * operand preparation, scratch sizing); the second records it as one CUDA graph and replays it;
+ * later calls replay the graph while no plan's buffers change (npf_set_tensor of the same shape
+ * and npf_set_modes keep them; options and new shapes do not). Plans' own streams and memory
+ * budgets are not used:
+ * the batch splits 80% of the free device memory over its streams (a plan's smaller budget is
+ * kept). Returns after all outputs are written; on error no output is guaranteed. Calls are
+ * serialised by a process-wide lock. */
 int npf_batch_compute(int count, npf_handle* const* plans, const int* orders,
                       npf_c128* const* outs);
+
+/* The tile width the autotuner chose for (n, order, precision, slices as set on the plan (0 =
+ * the precision's default), divide), or 0 if that key has not been tuned in this process. */
+int npf_tuned_tile(int n, int order, int precision, int slices, int divide);
 
 /* Message / code of the last error raised on this host thread. */
 const char* npf_last_error(void);

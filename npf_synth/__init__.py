@@ -205,3 +205,54 @@ def batch_systems(count: int = 256, seed: int = 0, n_lo: int = 20, n_hi: int = 8
         sysm.tensors[N] = random_packed_tensor(n, N, seed * 100003 + b * 7 + N)
         out.append((sysm, N))
     return out
+
+
+# ----------------------------------------------------------------------------------------
+# Parameterised family of operating points (learned-surrogate workload).
+# ----------------------------------------------------------------------------------------
+
+@dataclass
+class OperatingPointFamily:
+    """A1(p) = A0 + (s - 1) A_load + sum_c (g_c - 1) A_ctrl[c] for p = (s, g_1, g_2, g_3); the
+    Taylor tensors do not depend on p."""
+    n: int
+    A0: np.ndarray           # real [n, n]
+    A_load: np.ndarray       # real [n, n]
+    A_ctrl: np.ndarray       # real [3, n, n]
+    tensors: dict            # order -> packed float64
+    lo: np.ndarray           # [4] parameter lower bounds
+    hi: np.ndarray           # [4] parameter upper bounds
+    p0: np.ndarray           # [4] nominal operating point
+
+    def A(self, p) -> np.ndarray:
+        p = np.asarray(p, dtype=np.float64)
+        return (self.A0 + (p[0] - 1.0) * self.A_load
+                + np.tensordot(p[1:] - 1.0, self.A_ctrl, axes=1))
+
+
+def surrogate_family(n: int = 40, seed: int = 0, orders=(2, 3),
+                     load_scale: float = 0.05, ctrl_scale: float = 0.05) -> OperatingPointFamily:
+    """n states in n/4 generator-like blocks (as config_blocks). The load matrix perturbs every
+    4x4 diagonal block with N(0, load_scale) entries; controller c perturbs the diagonal blocks
+    b with b % 3 == c with N(0, ctrl_scale) entries. Load scale s ~ U[0.6, 1.2], gains
+    g_c ~ U[0.5, 2]; nominal point (1, 1, 1, 1). Tensors A_N 30% nonzero N(0, 1)."""
+    base = modal_system(n, seed, block=4, coupling=0.1, coupling_density=0.10)
+    rng = np.random.default_rng(seed + 104729)
+    nb = n // 4
+    A_load = np.zeros((n, n))
+    A_ctrl = np.zeros((3, n, n))
+    for b in range(nb):
+        sl = slice(4 * b, 4 * b + 4)
+        A_load[sl, sl] = load_scale * rng.standard_normal((4, 4))
+        A_ctrl[b % 3][sl, sl] = ctrl_scale * rng.standard_normal((4, 4))
+    tensors = {N: random_packed_tensor(n, N, seed * 1000 + 500 + N) for N in orders}
+    return OperatingPointFamily(n=n, A0=base.A1, A_load=A_load, A_ctrl=A_ctrl, tensors=tensors,
+                                lo=np.array([0.6, 0.5, 0.5, 0.5]),
+                                hi=np.array([1.2, 2.0, 2.0, 2.0]),
+                                p0=np.ones(4))
+
+
+def operating_points(fam: OperatingPointFamily, count: int, seed: int) -> np.ndarray:
+    """`count` parameter vectors drawn uniformly from the family's box, [count, 4]."""
+    rng = np.random.default_rng(seed)
+    return fam.lo + (fam.hi - fam.lo) * rng.random((count, 4))

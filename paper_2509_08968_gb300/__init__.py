@@ -53,6 +53,18 @@ def load():
     lib.npf_plan.restype = vp
     lib.npf_plan.argtypes = [ci, ci, vp, vp, vp, sz]
     lib.npf_set_tensor.argtypes = [vp, ci, vp]
+    lib.npf_set_modes.argtypes = [vp, vp, vp, vp]
+    lib.npf_mlp_create.restype = vp
+    lib.npf_mlp_create.argtypes = [ci, ci, vp, vp, vp]
+    lib.npf_mlp_param_count.restype = i64
+    lib.npf_mlp_param_count.argtypes = [vp]
+    lib.npf_mlp_get_weights.argtypes = [vp, vp]
+    lib.npf_mlp_forward.argtypes = [vp, ci, vp, vp]
+    lib.npf_mlp_loss_grad.argtypes = [vp, ci, vp, vp, vp, vp]
+    lib.npf_mlp_train.argtypes = [vp, ci, vp, vp, ci, ci, cd, ctypes.c_uint64, vp]
+    lib.npf_mlp_predict.argtypes = [vp, ci, vp, vp, vp, cd, vp, vp, vp]
+    lib.npf_mlp_destroy.argtypes = [vp]
+    lib.npf_mlp_destroy.restype = None
     lib.npf_compute.argtypes = [vp, ci, vp]
     lib.npf_destroy.argtypes = [vp]
     lib.npf_destroy.restype = None
@@ -67,6 +79,8 @@ def load():
     lib.npf_get_profile.argtypes = [vp, ci, vp, vp, vp, ci]
     lib.npf_launch_count.restype = i64
     lib.npf_launch_count.argtypes = []
+    lib.npf_tuned_tile.restype = ci
+    lib.npf_tuned_tile.argtypes = [ci, ci, ci, ci, ci]
     _lib = lib
     return lib
 
@@ -129,6 +143,12 @@ class Plan:
         self.set_option(OPT_STREAM, float(stream))
 
     # -- data ------------------------------------------------------------------------------
+    def set_modes(self, lam, U, V):
+        """Replace the modal data by another system of the same size (buffers kept)."""
+        if not _is_torch(lam):
+            lam, U, V = _host_c128(lam), _host_c128(U), _host_c128(V)
+        _check(load().npf_set_modes(self._h, _ptr(lam), _ptr(U), _ptr(V)))
+
     def set_tensor(self, order, coeffs):
         """Packed symmetric order-`order` tensor [n, C(n+order-1, order)] float64."""
         if not _is_torch(coeffs):
@@ -214,3 +234,9 @@ def alg1_batches(n_dim, n_s, m_limit_gb, bytes_per_elem=8):
 
 def launch_count():
     return int(load().npf_launch_count())
+
+
+def tuned_tile(n, order, precision="split_bf16", slices=0, divide=True):
+    """Tile width the autotuner chose for this key in this process (0 = not tuned yet)."""
+    pr = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return int(load().npf_tuned_tile(n, order, pr, slices, 1 if divide else 0))

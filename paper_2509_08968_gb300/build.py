@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["npf_api.cu", "k_common.cu", "k_fp64.cu", "k_split.cu"]
+SOURCES = ["npf_api.cu", "k_common.cu", "k_fp64.cu", "k_split.cu", "k_mlp.cu"]
 HEADERS = ["npf_internal.h", "k_device.cuh", "k_tc.cuh"]
 
 
@@ -35,7 +35,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [
-        os.path.join(HERE, "..", "include", "npf.h")]
+        os.path.join(HERE, "..", "include", "npf.h"),
+        os.path.join(HERE, "..", "include", "npf_mlp.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "-Xptxas", "-v" if verbose else "-O3", "--expt-relaxed-constexpr"]
     jobs = []

@@ -11,6 +11,7 @@ namespace npf {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(); }
 
 [[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
@@ -43,7 +44,7 @@ size_t effective_budget(const Plan& p)
     if (p.mem_budget) return p.mem_budget;
     size_t fr = 0, tot = 0;
     NPF_CUDA(cudaMemGetInfo(&fr, &tot));
-    return (size_t)(0.8 * (double)(fr + p.arena.cap));
+    return (size_t)(0.8 * (double)(fr + const_cast<Plan&>(p).scratch().cap));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -82,7 +83,10 @@ LaunchScope::LaunchScope(Profiler* p_, const char* n_, cudaStream_t s_) : p(p_),
 }
 LaunchScope::~LaunchScope()
 {
-    note_launch();
+    // a launch recorded into a graph is counted when the graph is replayed
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cudaGetLastError();
+    if (cs == cudaStreamCaptureStatusNone) note_launch();
     if (p && e0) {
         try { p->end(name, s, e0); } catch (...) {}
     }
@@ -92,6 +96,7 @@ LaunchScope::~LaunchScope()
 void Arena::reserve(size_t bytes)
 {
     if (bytes <= cap) return;
+    if (frozen) fail(NPF_ERR_OOM, "scratch would have to grow while work is recorded into a graph");
     release();
     void* ptr = nullptr;
     cudaError_t e = cudaMalloc(&ptr, bytes);

@@ -202,8 +202,9 @@ void fp64_term(Plan& p, int N, double2* d_out)
     const size_t per_nb = (2 * (size_t)nN + (size_t)nN / n) * sizeof(double2);
     int nb = (int)std::min<size_t>((size_t)n, budget / per_nb);
     if (nb < 1) fail(NPF_ERR_OOM, "memory budget too small for one output-index batch");
-    p.arena.reserve(per_nb * nb);
-    double2* bufA = (double2*)p.arena.base;
+    Arena& ar = p.scratch();
+    ar.reserve(per_nb * nb);
+    double2* bufA = (double2*)ar.base;
     double2* bufB = bufA + (size_t)nb * nN;
     double2* bufC = bufB + (size_t)nb * nN;
 
@@ -263,8 +264,9 @@ void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out)
 {
     const int n = p.n;
     const int64_t nN1 = ipow64(n, N - 1);
-    p.arena.reserve(2 * (size_t)n * nN1 * sizeof(double2));
-    double2* X = (double2*)p.arena.base;
+    Arena& ar = p.scratch();
+    ar.reserve(2 * (size_t)n * nN1 * sizeof(double2));
+    double2* X = (double2*)ar.base;
     double2* Y = X + (size_t)n * nN1;
     DivideArgs none = divide_args(p, N);
     {

@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             red[part * 64 + cl] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
             asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
             const int qc = qbase + cl;
-            if (ok && part == 0 && qc < n) {
+            if (ok && part == 0 && cl < bnc && qc < n) {   // the tile holds bnc columns
                 dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
                 for (int pp = 0; pp < 4; ++pp) {
                     const float4 g = red[pp * 64 + cl];
@@ -931,6 +931,46 @@ static void set_smem_attrs()
     done = true;
 }
 
+// Device copy of a host vector: a new buffer when `dst` is null, else overwritten in place.
+template <class D, class T>
+static void put(D*& dst, const std::vector<T>& v)
+{
+    if (!dst) {
+        dst = reinterpret_cast<D*>(upload(v));
+        return;
+    }
+    NPF_CUDA(cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+// Slices of Phi, Psi and Psi^T and the double-float Psi, from the plan's modal data.
+static void fill_fixed(Plan& p, SplitOperand* so)
+{
+    const int n = p.n, S = so->S;
+    std::vector<double2> U(n * n), V(n * n);
+    NPF_CUDA(cudaMemcpy(U.data(), p.d_U, U.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    NPF_CUDA(cudaMemcpy(V.data(), p.d_V, V.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    std::vector<uint16_t> planes;
+    std::vector<int> ex;
+    // Phi: K index a, column p: phi_{a p}
+    build_fixed(n, S, true, [&](int a, int c) { return U[(size_t)a * n + c]; }, planes, ex);
+    put(so->phi, planes);
+    put(so->phi_e, ex);
+    // Psi for the upper-index contraction: real K index j, column i: psi_{i j}
+    build_fixed(n, S, false, [&](int j, int i) { return V[(size_t)i * n + j]; }, planes, ex);
+    put(so->psir, planes);
+    put(so->psir_e, ex);
+    // Psi^T rows k for the reduction: complex K index p, row k: psi_{p k}
+    build_fixed(n, S, true, [&](int pidx, int k) { return V[(size_t)pidx * n + k]; }, planes, ex);
+    put(so->red, planes);
+    put(so->red_e, ex);
+    std::vector<float4> pdf((size_t)n * n);
+    for (size_t t = 0; t < pdf.size(); ++t) {
+        const float rh = (float)V[t].x, ih = (float)V[t].y;
+        pdf[t] = make_float4(rh, (float)(V[t].x - rh), ih, (float)(V[t].y - ih));
+    }
+    put(so->psi_df, pdf);
+}
+
 static SplitOperand& prepare(Plan& p)
 {
     const int S = default_slices(p);
@@ -940,33 +980,15 @@ static SplitOperand& prepare(Plan& p)
     SplitOperand* so = new SplitOperand();
     p.split = so;
     so->S = S;
-    const int n = p.n;
-    std::vector<double2> U(n * n), V(n * n);
-    NPF_CUDA(cudaMemcpy(U.data(), p.d_U, U.size() * sizeof(double2), cudaMemcpyDeviceToHost));
-    NPF_CUDA(cudaMemcpy(V.data(), p.d_V, V.size() * sizeof(double2), cudaMemcpyDeviceToHost));
-    std::vector<uint16_t> planes;
-    std::vector<int> ex;
-    // Phi: K index a, column p: phi_{a p}
-    build_fixed(n, S, true, [&](int a, int c) { return U[(size_t)a * n + c]; }, planes, ex);
-    so->phi = (__nv_bfloat16*)upload(planes);
-    so->phi_e = upload(ex);
-    // Psi for the upper-index contraction: real K index j, column i: psi_{i j}
-    build_fixed(n, S, false, [&](int j, int i) { return V[(size_t)i * n + j]; }, planes, ex);
-    so->psir = (__nv_bfloat16*)upload(planes);
-    so->psir_e = upload(ex);
-    // Psi^T rows k for the reduction: complex K index p, row k: psi_{p k}
-    build_fixed(n, S, true, [&](int pidx, int k) { return V[(size_t)pidx * n + k]; }, planes, ex);
-    so->red = (__nv_bfloat16*)upload(planes);
-    so->red_e = upload(ex);
-    std::vector<float4> pdf((size_t)n * n);
-    for (size_t t = 0; t < pdf.size(); ++t) {
-        const float rh = (float)V[t].x, ih = (float)V[t].y;
-        pdf[t] = make_float4(rh, (float)(V[t].x - rh), ih, (float)(V[t].y - ih));
-    }
-    so->psi_df = upload(pdf);
+    fill_fixed(p, so);
     NPF_CUDA(cudaMalloc(&so->err, sizeof(int)));
     NPF_CUDA(cudaMemset(so->err, 0, sizeof(int)));
     return *so;
+}
+
+void split_refresh_modes(Plan& p)
+{
+    if (p.split) fill_fixed(p, p.split);   // same n and S: the buffers (and graphs) stay valid
 }
 
 // A^T digit planes of the packed tensor (part of the tensor upload; redone when the tensor or the
@@ -977,10 +999,14 @@ static void prepare_tensor(Plan& p, SplitOperand& so, int N)
     if (so.at[N] && so.at_src[N] == p.d_tensor[N]) return;
     const int64_t P = p.packed_count[N];
     const int64_t rows = (P + NP - 1) / NP * NP;
-    cudaFree(so.at[N]);
-    cudaFree(so.at_e[N]);
-    NPF_CUDA(cudaMalloc(&so.at[N], (size_t)S * rows * NP * 2));
-    NPF_CUDA(cudaMalloc(&so.at_e[N], (size_t)rows * sizeof(int)));
+    if (!so.at[N] || so.at_rows[N] != rows) {   // same shape: keep the buffers (graphs hold them)
+        cudaFree(so.at[N]);
+        cudaFree(so.at_e[N]);
+        so.at[N] = nullptr;
+        so.at_e[N] = nullptr;
+        NPF_CUDA(cudaMalloc(&so.at[N], (size_t)S * rows * NP * 2));
+        NPF_CUDA(cudaMalloc(&so.at_e[N], (size_t)rows * sizeof(int)));
+    }
     NPF_CUDA(cudaMemsetAsync(so.at[N], 0, (size_t)S * rows * NP * 2, p.stream));
     {
         LaunchScope ls(&p.prof, "split_prepare_tensor", p.stream);
@@ -990,6 +1016,11 @@ static void prepare_tensor(Plan& p, SplitOperand& so, int N)
     }
     so.at_rows[N] = rows;
     so.at_src[N] = p.d_tensor[N];
+}
+
+const void* split_tensor_planes(const Plan& p, int N)
+{
+    return p.split ? p.split->at[N] : nullptr;
 }
 
 void split_prepare_tensor(Plan& p, int N)
@@ -1071,7 +1102,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     SplitOperand& so = prepare(p);
     set_smem_attrs<S>();
     prepare_tensor<S>(p, so, N);
-    NPF_CUDA(cudaMemsetAsync(so.err, 0, sizeof(int), p.stream));
+    int* const err = p.err_override ? p.err_override : so.err;   // a batch zeroes and checks its own
+    if (!p.err_override) NPF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), p.stream));
     const int n = p.n;
     const int64_t P = p.packed_count[N];
     const int64_t Prows = so.at_rows[N];
@@ -1089,8 +1121,9 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     const int64_t t_rows = (int64_t)ib * npN1;
     const size_t tbytes = (size_t)t_rows * KP * 2 * S;
     const size_t ebytes = (size_t)t_rows * 4;
-    p.arena.reserve(s_bytes + rec_bytes + 2 * (tbytes + ebytes) + 8 * 256 + 1024);
-    uint8_t* base = (uint8_t*)p.arena.base;
+    Arena& ar = p.scratch();
+    ar.reserve(s_bytes + rec_bytes + 2 * (tbytes + ebytes) + 8 * 256 + 1024);
+    uint8_t* base = (uint8_t*)ar.base;
     auto take = [&](size_t bytes) { uint8_t* r = base; base += (bytes + 255) & ~(size_t)255; return r; };
     double2* Sd = (double2*)take(s_bytes);
     uint4* rec = (uint4*)take(rec_bytes);
@@ -1117,7 +1150,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     base0.invfact = 1.0 / factorial(N);
     base0.eps = p.eps;
     base0.divide = p.divide;
-    base0.err = so.err;
+    base0.err = err;
     base0.bnc = p.tile_n;
     base0.ncol_tiles = NP / p.tile_n;
     if (slab)
@@ -1127,7 +1160,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     {
         RowArgs a = base0;
         a.a_rows = (int)Prows;
-        a.kch = NP / BK;
+        a.kch = (n + BK - 1) / BK;   // K = j < n: chunks past n hold zeros only
         a.ea = so.at_e[N];
         a.ea_shift = 0;
         a.eb = so.psir_e;
@@ -1159,7 +1192,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
         for (int c = 1; c <= N; ++c) {
             RowArgs a = base0;
             a.a_rows = (int)t_rows;
-            a.kch = KP / BK;
+            a.kch = (2 * n + BK - 1) / BK;   // K' = 2 p + re/im < 2 n
             a.ea = c == 1 ? sE + i0 : E[cb];
             a.ea_shift = c == 1 ? 7 * (N - 1) : 0;
             a.eb = so.phi_e;
@@ -1187,7 +1220,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
         // ---- reduction: rows c' = (i, p_1..p_{N-1}), K = p_N, columns k (Psi^T)
         RowArgs a = base0;
         a.a_rows = (int)t_rows;
-        a.kch = KP / BK;
+        a.kch = (2 * n + BK - 1) / BK;   // K' = 2 p + re/im < 2 n
         a.ea = E[cb];
         a.ea_shift = 0;
         a.eb = so.red_e;
@@ -1201,8 +1234,9 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
         a.out_f64 = d_out;
         launch_rows<S, EPI_REDUCE>(p, "split_reduce", *tT[cb], tRed, a);
     }
+    if (p.err_override) return;   // the batch reads the shared flag after its graph has run
     int herr = 0;
-    NPF_CUDA(cudaMemcpyAsync(&herr, so.err, sizeof(int), cudaMemcpyDeviceToHost, p.stream));
+    NPF_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, p.stream));
     NPF_CUDA(cudaStreamSynchronize(p.stream));
     if (herr) fail(NPF_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
 }

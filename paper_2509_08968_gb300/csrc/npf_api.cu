@@ -1,7 +1,13 @@
 // npf_api.cu -- the C ABI (include/npf.h): plans, tensor upload, compute, options, errors,
 // the Algorithm 1 batch-sizing rule and kernel profiling.
+#include <algorithm>
+#include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <limits>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,10 +77,117 @@ void free_plan(Plan& p)
     p.arena.release();
 }
 
+std::atomic<uint64_t> g_next_plan_id{0};
+
+// Validate (max |V U - I| <= NPF_INVERSE_TOL) and copy the modal data into the plan's buffers.
+void load_modes(Plan& p, const npf_c128* eigvals, const npf_c128* U, const npf_c128* V)
+{
+    const int n = p.n;
+    const size_t nn = (size_t)n * n;
+    // host copies for validation and the transposed Psi
+    std::vector<double2> hU(nn), hV(nn), hVt(nn);
+    NPF_CUDA(cudaMemcpy(hU.data(), U, nn * sizeof(double2), cudaMemcpyDefault));
+    NPF_CUDA(cudaMemcpy(hV.data(), V, nn * sizeof(double2), cudaMemcpyDefault));
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) hVt[(size_t)k * n + i] = hV[(size_t)i * n + k];
+    // max |V U - I|
+    double worst = 0.0;
+    {
+        std::vector<double2> row(n);
+        for (int i = 0; i < n; ++i) {
+            for (int c = 0; c < n; ++c) row[c] = make_double2(0, 0);
+            for (int j = 0; j < n; ++j) {
+                const double2 v = hV[(size_t)i * n + j];
+                const double2* u = &hU[(size_t)j * n];
+                for (int c = 0; c < n; ++c) {
+                    row[c].x += v.x * u[c].x - v.y * u[c].y;
+                    row[c].y += v.x * u[c].y + v.y * u[c].x;
+                }
+            }
+            for (int c = 0; c < n; ++c) {
+                const double re = row[c].x - (c == i ? 1.0 : 0.0);
+                worst = std::fmax(worst, std::hypot(re, row[c].y));
+            }
+        }
+    }
+    if (!(worst <= NPF_INVERSE_TOL))
+        npf::fail(NPF_ERR_NOT_INVERSE,
+                  "max|V U - I| = " + std::to_string(worst) + " exceeds NPF_INVERSE_TOL");
+    NPF_CUDA(cudaMemcpy(p.d_U, hU.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
+    NPF_CUDA(cudaMemcpy(p.d_V, hV.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
+    NPF_CUDA(cudaMemcpy(p.d_Vt, hVt.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
+    NPF_CUDA(cudaMemcpy(p.d_lam, eigvals, n * sizeof(double2), cudaMemcpyDefault));
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Tile-width autotuner of the tensor-core forms. Key: (n, order, precision, slices, divide).
+// On the first term of an untuned key every candidate width runs the plan's own term once
+// untimed (preparation, scratch) and once timed with CUDA events on the plan's stream; the
+// fastest is kept for the life of the process.
+// ---------------------------------------------------------------------------------------
+using TuneKey = std::array<int, 5>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+constexpr int kTileCandidates[3] = {16, 32, 64};
+
+TuneKey tune_key(const Plan& p, int N) { return {p.n, N, p.precision, p.slices, p.divide}; }
+
+int tuned_tile(Plan& p, int N)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const TuneKey key = tune_key(p, N);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+    if (p.capturing) npf::fail(NPF_ERR_ARG, "tile width not tuned before graph capture");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NPF_CUDA(cudaEventCreate(&e0));
+    NPF_CUDA(cudaEventCreate(&e1));
+    float best = std::numeric_limits<float>::infinity();
+    int best_tile = 64;
+    try {
+        for (int t : kTileCandidates) {
+            p.tile_n = t;
+            npf::split_term(p, N, p.d_psiN[N]);
+            NPF_CUDA(cudaEventRecord(e0, p.stream));
+            npf::split_term(p, N, p.d_psiN[N]);
+            NPF_CUDA(cudaEventRecord(e1, p.stream));
+            NPF_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            NPF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_tile = t; }
+        }
+    } catch (...) {
+        p.tile_n = 0;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    p.tile_n = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_tuned[key] = best_tile;
+    return best_tile;
+}
+
 void compute_term(Plan& p, int N, double2* out)
 {
-    if (p.precision == NPF_PREC_FP64) npf::fp64_term(p, N, out);
-    else npf::split_term(p, N, out);
+    if (p.precision == NPF_PREC_FP64) {
+        npf::fp64_term(p, N, out);
+        return;
+    }
+    if (p.tile_n != 0) {
+        npf::split_term(p, N, out);
+        return;
+    }
+    p.tile_n = tuned_tile(p, N);
+    try {
+        npf::split_term(p, N, out);
+    } catch (...) {
+        p.tile_n = 0;
+        throw;
+    }
+    p.tile_n = 0;
 }
 
 // Psi_m for every order 2..order that has a tensor, summed into d_sum; NPF into d_npf.
@@ -88,6 +201,230 @@ void compute_npf(Plan& p, int order)
         npf::launch_add(p, p.d_sum, p.d_psiN[m], nn);
     }
     npf::launch_finish(p, order >= 2 ? p.d_sum : nullptr, p.d_npf);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched execution: independent systems issued as one CUDA graph.
+//
+// Scheduler: the systems are placed on kWorkers library-owned streams by longest-processing-
+// time-first (estimated work n^(N+2) for order N >= 2, n^2 for order 1), so that the graph's
+// branches finish close together. Plans on one stream run one after another and share that
+// stream's scratch arena, sized by the first (eager) pass under a budget of 80% of the free
+// device memory split evenly over the streams. The eager pass also tunes tile widths and prepares
+// every operand; the same work is then recorded into a graph (fork/join over the worker
+// streams), instantiated once and cached under the plans' ids, generations and orders, and the
+// graph is replayed on every call with the same key. A shared device flag collects the
+// bounded-wait errors of every kernel in the graph and is read after the replay.
+// ---------------------------------------------------------------------------------------
+constexpr int kWorkers = 8;
+constexpr size_t kGraphCacheSize = 8;
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    uint64_t stamp = 0;
+};
+
+struct BatchPool {
+    cudaStream_t origin = nullptr;
+    cudaStream_t ws[kWorkers] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kWorkers] = {};
+    npf::Arena arena[kWorkers];
+    int* d_err = nullptr;
+    std::map<std::string, GraphEntry> graphs;
+    std::map<std::string, size_t> seen;   // lists run once eagerly, with the budget they used
+    uint64_t clock = 0;
+
+    void init()
+    {
+        if (origin) return;
+        NPF_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+        for (int w = 0; w < kWorkers; ++w) {
+            NPF_CUDA(cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking));
+            NPF_CUDA(cudaEventCreateWithFlags(&join[w], cudaEventDisableTiming));
+        }
+        NPF_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        NPF_CUDA(cudaMalloc(&d_err, sizeof(int)));
+        NPF_CUDA(cudaMemset(d_err, 0, sizeof(int)));
+    }
+    void drop_graphs()
+    {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+        graphs.clear();
+    }
+};
+
+std::mutex g_batch_mu;
+std::map<int, BatchPool> g_pools;   // per device; kept for the life of the process
+
+// Temporarily routes one plan's work to a worker stream / arena / budget / error flag.
+struct PlanRoute {
+    Plan& p;
+    cudaStream_t stream;
+    size_t budget;
+    bool prof;
+    PlanRoute(Plan& p_, cudaStream_t s, npf::Arena* a, size_t bud, bool capture, int* err)
+        : p(p_), stream(p_.stream), budget(p_.mem_budget), prof(p_.prof.enabled)
+    {
+        p.stream = s;
+        p.shared_arena = a;
+        p.mem_budget = p.mem_budget ? std::min(p.mem_budget, bud) : bud;
+        p.capturing = capture;
+        p.err_override = err;
+        if (capture) p.prof.enabled = false;
+    }
+    ~PlanRoute()
+    {
+        p.stream = stream;
+        p.shared_arena = nullptr;
+        p.mem_budget = budget;
+        p.capturing = false;
+        p.err_override = nullptr;
+        p.prof.enabled = prof;
+    }
+};
+
+// Longest-processing-time-first placement of the systems on the worker streams.
+std::vector<int> schedule(int count, npf_handle* const* plans, const int* orders)
+{
+    std::vector<double> work(count);
+    for (int b = 0; b < count; ++b) {
+        const double n = plans[b]->p.n;
+        work[b] = orders[b] >= 2 ? std::pow(n, orders[b] + 2) : n * n;
+    }
+    std::vector<int> idx(count);
+    for (int b = 0; b < count; ++b) idx[b] = b;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::vector<double> load(kWorkers, 0.0);
+    std::vector<int> worker(count);
+    for (int b : idx) {
+        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        worker[b] = w;
+        load[w] += work[b];
+    }
+    return worker;
+}
+
+std::string batch_key(int dev, int count, npf_handle* const* plans, const int* orders)
+{
+    std::string k = std::to_string(dev);
+    for (int b = 0; b < count; ++b) {
+        const Plan& p = plans[b]->p;
+        k += ";" + std::to_string(p.id) + ":" + std::to_string(p.gen) + ":" +
+             std::to_string(orders[b]);
+    }
+    return k;
+}
+
+GraphEntry capture_batch(BatchPool& pool, int count, npf_handle* const* plans, const int* orders,
+                         const std::vector<int>& worker, size_t budget)
+{
+    NPF_CUDA(cudaStreamBeginCapture(pool.origin, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+        NPF_CUDA(cudaMemsetAsync(pool.d_err, 0, sizeof(int), pool.origin));
+        NPF_CUDA(cudaEventRecord(pool.fork, pool.origin));
+        for (int w = 0; w < kWorkers; ++w) NPF_CUDA(cudaStreamWaitEvent(pool.ws[w], pool.fork, 0));
+        for (int w = 0; w < kWorkers; ++w) pool.arena[w].frozen = true;
+        for (int b = 0; b < count; ++b) {
+            const int w = worker[b];
+            PlanRoute r(plans[b]->p, pool.ws[w], &pool.arena[w], budget, true, pool.d_err);
+            compute_npf(plans[b]->p, orders[b]);
+        }
+        for (int w = 0; w < kWorkers; ++w) {
+            pool.arena[w].frozen = false;
+            NPF_CUDA(cudaEventRecord(pool.join[w], pool.ws[w]));
+            NPF_CUDA(cudaStreamWaitEvent(pool.origin, pool.join[w], 0));
+        }
+        NPF_CUDA(cudaStreamEndCapture(pool.origin, &graph));
+    } catch (...) {
+        for (int w = 0; w < kWorkers; ++w) pool.arena[w].frozen = false;
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(pool.origin, &g);   // leave capture mode whatever happened
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        throw;
+    }
+    GraphEntry e;
+    size_t num = 0;
+    NPF_CUDA(cudaGraphGetNodes(graph, nullptr, &num));
+    std::vector<cudaGraphNode_t> nodes(num);
+    if (num) NPF_CUDA(cudaGraphGetNodes(graph, nodes.data(), &num));
+    for (size_t t = 0; t < num; ++t) {
+        cudaGraphNodeType ty;
+        NPF_CUDA(cudaGraphNodeGetType(nodes[t], &ty));
+        if (ty == cudaGraphNodeTypeKernel) ++e.kernels;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    NPF_CUDA(ie);
+    return e;
+}
+
+void batch_run(int count, npf_handle* const* plans, const int* orders, npf_c128* const* outs)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    int dev = 0;
+    NPF_CUDA(cudaGetDevice(&dev));
+    BatchPool& pool = g_pools[dev];
+    pool.init();
+    const std::string key = batch_key(dev, count, plans, orders);
+    auto it = pool.graphs.find(key);
+    if (it == pool.graphs.end()) {
+        const std::vector<int> worker = schedule(count, plans, orders);
+        auto sn = pool.seen.find(key);
+        if (sn == pool.seen.end()) {
+            // first sighting of this list: run it eagerly (tile tuning, operand preparation,
+            // scratch sizing); its outputs are the result. A list seen again is recorded.
+            size_t fr = 0, tot = 0, held = 0;
+            NPF_CUDA(cudaMemGetInfo(&fr, &tot));
+            for (int w = 0; w < kWorkers; ++w) held += pool.arena[w].cap;
+            const size_t budget = (size_t)(0.8 * (double)(fr + held) / kWorkers);
+            void* bases[kWorkers];
+            for (int w = 0; w < kWorkers; ++w) bases[w] = pool.arena[w].base;
+            for (int b = 0; b < count; ++b) {
+                const int w = worker[b];
+                PlanRoute r(plans[b]->p, pool.ws[w], &pool.arena[w], budget, false, nullptr);
+                compute_npf(plans[b]->p, orders[b]);
+            }
+            for (int w = 0; w < kWorkers; ++w) NPF_CUDA(cudaStreamSynchronize(pool.ws[w]));
+            bool moved = false;
+            for (int w = 0; w < kWorkers; ++w) moved |= bases[w] != pool.arena[w].base;
+            if (moved) pool.drop_graphs();   // cached graphs address the old scratch
+            if (pool.seen.size() >= 256) pool.seen.clear();
+            pool.seen[key] = budget;
+            for (int b = 0; b < count; ++b) {
+                const Plan& p = plans[b]->p;
+                NPF_CUDA(cudaMemcpyAsync(outs[b], p.d_npf, (size_t)p.n * p.n * sizeof(double2),
+                                         cudaMemcpyDefault, pool.origin));
+            }
+            NPF_CUDA(cudaStreamSynchronize(pool.origin));
+            return;
+        }
+        if (pool.graphs.size() >= kGraphCacheSize) {
+            auto old = pool.graphs.begin();
+            for (auto g = pool.graphs.begin(); g != pool.graphs.end(); ++g)
+                if (g->second.stamp < old->second.stamp) old = g;
+            cudaGraphExecDestroy(old->second.exec);
+            pool.graphs.erase(old);
+        }
+        // same schedule and budget as the eager run: the scratch it sized suffices
+        GraphEntry e = capture_batch(pool, count, plans, orders, worker, sn->second);
+        it = pool.graphs.emplace(key, e).first;
+    }
+    it->second.stamp = ++pool.clock;
+    NPF_CUDA(cudaGraphLaunch(it->second.exec, pool.origin));
+    npf::note_launches(it->second.kernels);
+    for (int b = 0; b < count; ++b) {
+        const Plan& p = plans[b]->p;
+        NPF_CUDA(cudaMemcpyAsync(outs[b], p.d_npf, (size_t)p.n * p.n * sizeof(double2),
+                                 cudaMemcpyDefault, pool.origin));
+    }
+    int herr = 0;
+    NPF_CUDA(cudaMemcpyAsync(&herr, pool.d_err, sizeof(int), cudaMemcpyDeviceToHost, pool.origin));
+    NPF_CUDA(cudaStreamSynchronize(pool.origin));
+    if (herr) npf::fail(NPF_ERR_TIMEOUT, "a tensor-core pipeline wait gave up inside the batch");
 }
 
 }  // namespace
@@ -122,6 +459,7 @@ npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* 
         p.n = n;
         p.Nmax = N_max;
         p.mem_budget = mem_budget;
+        p.id = ++g_next_plan_id;
         const size_t nn = (size_t)n * n;
         NPF_CUDA(cudaMalloc(&p.d_lam, n * sizeof(double2)));
         NPF_CUDA(cudaMalloc(&p.d_U, nn * sizeof(double2)));
@@ -133,39 +471,7 @@ npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* 
             NPF_CUDA(cudaMalloc(&p.d_psiN[N], nn * sizeof(double2)));
             p.packed_count[N] = npf::packed_count(n, N);
         }
-        // host copies for validation and the transposed Psi
-        std::vector<double2> hU(nn), hV(nn), hVt(nn);
-        NPF_CUDA(cudaMemcpy(hU.data(), U, nn * sizeof(double2), cudaMemcpyDefault));
-        NPF_CUDA(cudaMemcpy(hV.data(), V, nn * sizeof(double2), cudaMemcpyDefault));
-        for (int i = 0; i < n; ++i)
-            for (int k = 0; k < n; ++k) hVt[(size_t)k * n + i] = hV[(size_t)i * n + k];
-        // max |V U - I|
-        double worst = 0.0;
-        {
-            std::vector<double2> row(n);
-            for (int i = 0; i < n; ++i) {
-                for (int c = 0; c < n; ++c) row[c] = make_double2(0, 0);
-                for (int j = 0; j < n; ++j) {
-                    const double2 v = hV[(size_t)i * n + j];
-                    const double2* u = &hU[(size_t)j * n];
-                    for (int c = 0; c < n; ++c) {
-                        row[c].x += v.x * u[c].x - v.y * u[c].y;
-                        row[c].y += v.x * u[c].y + v.y * u[c].x;
-                    }
-                }
-                for (int c = 0; c < n; ++c) {
-                    const double re = row[c].x - (c == i ? 1.0 : 0.0);
-                    worst = std::fmax(worst, std::hypot(re, row[c].y));
-                }
-            }
-        }
-        if (!(worst <= NPF_INVERSE_TOL))
-            npf::fail(NPF_ERR_NOT_INVERSE,
-                      "max|V U - I| = " + std::to_string(worst) + " exceeds NPF_INVERSE_TOL");
-        NPF_CUDA(cudaMemcpy(p.d_U, hU.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
-        NPF_CUDA(cudaMemcpy(p.d_V, hV.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
-        NPF_CUDA(cudaMemcpy(p.d_Vt, hVt.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
-        NPF_CUDA(cudaMemcpy(p.d_lam, eigvals, n * sizeof(double2), cudaMemcpyDefault));
+        load_modes(p, eigvals, U, V);
         npf::build_cnt_table(p);
     });
     if (rc != NPF_OK) {
@@ -175,6 +481,17 @@ npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* 
     return h;
 }
 
+int npf_set_modes(npf_handle* h, const npf_c128* eigvals, const npf_c128* U, const npf_c128* V)
+{
+    return guarded([&] {
+        if (!h || !eigvals || !U || !V) npf::fail(NPF_ERR_ARG, "null argument");
+        Plan& p = h->p;
+        NPF_CUDA(cudaStreamSynchronize(p.stream));
+        load_modes(p, eigvals, U, V);
+        npf::split_refresh_modes(p);   // tensor-core forms: slices of Phi and Psi, in place
+    });
+}
+
 int npf_set_tensor(npf_handle* h, int order, const double* coeffs)
 {
     return guarded([&] {
@@ -182,9 +499,13 @@ int npf_set_tensor(npf_handle* h, int order, const double* coeffs)
         Plan& p = h->p;
         if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
         const size_t bytes = (size_t)p.n * p.packed_count[order] * sizeof(double);
+        const void* before[2] = {p.d_tensor[order], npf::split_tensor_planes(p, order)};
         if (!p.d_tensor[order]) NPF_CUDA(cudaMalloc(&p.d_tensor[order], bytes));
         copy_in(p.d_tensor[order], coeffs, bytes, p.stream);
         npf::split_prepare_tensor(p, order);   // tensor-core forms: digit planes of the upload
+        // recorded batch graphs stay valid while the device buffers they address do
+        if (before[0] != p.d_tensor[order] || before[1] != npf::split_tensor_planes(p, order))
+            ++p.gen;
         sync(p);
     });
 }
@@ -255,6 +576,7 @@ int npf_set_option(npf_handle* h, int key, double value)
     return guarded([&] {
         if (!h) npf::fail(NPF_ERR_ARG, "null handle");
         Plan& p = h->p;
+        ++p.gen;
         switch (key) {
         case NPF_OPT_PRECISION: {
             const int v = (int)value;
@@ -290,7 +612,8 @@ int npf_set_option(npf_handle* h, int key, double value)
             break;
         case NPF_OPT_TILE_N: {
             const int v = (int)value;
-            if (v != 16 && v != 32 && v != 64) npf::fail(NPF_ERR_ARG, "tile width must be 16, 32 or 64");
+            if (v != 0 && v != 16 && v != 32 && v != 64)
+                npf::fail(NPF_ERR_ARG, "tile width must be 0 (autotuned), 16, 32 or 64");
             p.tile_n = v;
             break;
         }
@@ -312,15 +635,19 @@ int npf_batch_compute(int count, npf_handle* const* plans, const int* orders,
             if (orders[b] < 1 || orders[b] > p.Nmax) npf::fail(NPF_ERR_ARG, "bad order in batch");
             if (orders[b] >= 2 && !p.d_tensor[orders[b]])
                 npf::fail(NPF_ERR_MISSING_TENSOR, "missing tensor in batch");
+            for (int c = 0; c < b; ++c)
+                if (plans[c] == plans[b]) npf::fail(NPF_ERR_ARG, "a plan appears twice in a batch");
         }
-        for (int b = 0; b < count; ++b) {
-            Plan& p = plans[b]->p;
-            compute_npf(p, orders[b]);
-            NPF_CUDA(cudaMemcpyAsync(outs[b], p.d_npf, (size_t)p.n * p.n * sizeof(double2),
-                                     cudaMemcpyDefault, p.stream));
-        }
-        for (int b = 0; b < count; ++b) sync(plans[b]->p);
+        if (count == 0) return;
+        batch_run(count, plans, orders, outs);
     });
+}
+
+int npf_tuned_tile(int n, int order, int precision, int slices, int divide)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(TuneKey{n, order, precision, slices, divide != 0});
+    return it == g_tuned.end() ? 0 : it->second;
 }
 
 // Algorithm 1: while the tensor exceeds the limit drop the outermost remaining dimension; if the

@@ -58,6 +58,7 @@ struct LaunchScope {
 struct Arena {
     void* base = nullptr;
     size_t cap = 0;
+    bool frozen = false;   // set while work is recorded into a CUDA graph: growing fails
     void reserve(size_t bytes);
     void release();
 };
@@ -73,7 +74,7 @@ struct Plan {
     int slices = 0;                // 0 = default for the precision
     double eps = 1e-8;
     int divide = 1;
-    int tile_n = 64;               // complex columns per tensor-core tile
+    int tile_n = 64;               // complex columns per tensor-core tile; 0 = autotuned
     size_t mem_budget = 0;         // 0 = 80% of free memory at compute time
     cudaStream_t stream = nullptr;
     Profiler prof;
@@ -96,6 +97,14 @@ struct Plan {
 
     Arena arena;
     SplitOperand* split = nullptr;
+
+    // batched execution (npf_batch_compute)
+    uint64_t id = 0;                // unique over the process, never reused
+    uint64_t gen = 0;               // bumped by every change of inputs or options
+    bool capturing = false;         // work is being recorded into a CUDA graph: no host syncs
+    Arena* shared_arena = nullptr;  // scratch shared by the plans issued on one stream
+    int* err_override = nullptr;    // device error flag shared by a batch (checked by the batch)
+    Arena& scratch() { return shared_arena ? *shared_arena : arena; }
 };
 
 int64_t packed_count(int n, int N);
@@ -117,6 +126,8 @@ void split_term(Plan& p, int N, double2* d_out);
 void split_slab(Plan& p, int N, const int* prefix, double2* d_out);
 void split_release(Plan& p);
 void split_prepare_tensor(Plan& p, int N);   // digit planes of a newly uploaded tensor
+const void* split_tensor_planes(const Plan& p, int N);   // device address of those planes
+void split_refresh_modes(Plan& p);   // new modal data of the same size: re-slice in place
 
 // ----------------------------------------------------------------------------------------
 // Small shared kernels (k_common.cu).
@@ -125,5 +136,6 @@ void launch_finish(Plan& p, const double2* d_sum, double2* d_npf);   // NPF = ph
 void launch_zero(Plan& p, double2* d, int64_t count);
 void launch_add(Plan& p, double2* acc, const double2* x, int64_t count);
 void build_cnt_table(Plan& p);
+void note_launches(int64_t k);   // k more kernels launched (graph replays)
 
 }  // namespace npf
