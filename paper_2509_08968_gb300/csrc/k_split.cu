@@ -57,7 +57,7 @@ constexpr int EXP_NONE = -4096;
 constexpr int TMEM_COLS = 512;
 constexpr int kErrTimeout = 1;
 constexpr int VEXP = 44;       // value = V * 2^(e_a + e_b - VEXP), V in units of 2^-30 of L0
-constexpr int EPI_WARPS = 8;   // epilogue warps (two per TMEM lane quarter)
+constexpr int EPI_WARPS = 16;  // epilogue warps (four per TMEM lane quarter)
 constexpr int ROW_THREADS = 64 + 32 * EPI_WARPS;
 
 // ---------------------------------------------------------------------------------------
@@ -155,13 +155,25 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b)
     return df_norm(p, e);
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
-// V * 2^sc as a double-float (relative error ~2^-48)
+// Exact sum a + b = s + e of two floats (Knuth's two-sum).
+__device__ __forceinline__ dfl two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+// V * 2^sc as a double-float (relative error ~2^-48) for |V| < 2^53. V is split into three
+// 21-bit pieces that are exact floats, so only 32-bit conversions are used: 64-bit integer <->
+// float conversions are slow on this GPU.
 __device__ __forceinline__ dfl df_from_i64(long long V, int sc)
 {
-    const float hi = __ll2float_rn(V);
-    const long long rem = V - __float2ll_rn(hi);
-    const float lo = __ll2float_rn(rem);
-    return {ldexpf(hi, sc), ldexpf(lo, sc)};
+    const int v2 = (int)(V >> 42);
+    const int v1 = (int)((V >> 21) & 0x1FFFFF);
+    const int v0 = (int)(V & 0x1FFFFF);
+    const dfl a = two_sum((float)v2 * 4398046511104.0f, (float)v1 * 2097152.0f);   // 2^42, 2^21
+    const dfl b = two_sum(a.hi, (float)v0);
+    const dfl r = df_norm(b.hi, b.lo + a.lo);
+    return {ldexpf(r.hi, sc), ldexpf(r.lo, sc)};
 }
 __device__ __forceinline__ double df_to_d(dfl a) { return (double)a.hi + (double)a.lo; }
 
@@ -171,7 +183,12 @@ __device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t 
     const long long a0 = (long long)__float2int_rz(__uint_as_float(l0));
     const long long a1 = (long long)__float2int_rn(__uint_as_float(l1) * 256.0f);
     const long long a2 = (long long)__float2int_rn(__uint_as_float(l2) * 65536.0f);
-    const long long a3 = (long long)__float2ll_rn(__uint_as_float(l3) * 1073741824.0f);
+    // rint(L3 * 2^30) with 32-bit conversions: the part above 2^20 truncated, the remainder
+    // (exact in FP32) rounded; the even multiple of 2^20 keeps the tie-to-even decision.
+    const float x3 = __uint_as_float(l3) * 1073741824.0f;
+    const int h3 = __float2int_rz(x3 * 9.5367431640625e-07f);                  // 2^-20
+    const int r3 = __float2int_rn(fmaf((float)h3, -1048576.0f, x3));            // exact remainder
+    const long long a3 = ((long long)h3 << 20) + r3;
     return (a0 << 30) + (a1 << 22) + (a2 << 14) + a3;
 }
 
@@ -179,16 +196,16 @@ __device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t 
 template <int S>
 struct Lev { static constexpr int N = S < 4 ? S : 4; };
 
-// Load 8 columns of every used level of one accumulator group (levels `stride` columns apart).
+// Load 4 columns of every used level of one accumulator group (levels `stride` columns apart).
 template <int S>
-__device__ __forceinline__ void load_levels(uint32_t taddr, int stride, uint32_t (&v)[4][8])
+__device__ __forceinline__ void load_levels(uint32_t taddr, int stride, uint32_t (&v)[4][4])
 {
 #pragma unroll
     for (int L = 0; L < 4; ++L) {
-        if (L < Lev<S>::N) tc::tmem_ld8(taddr + L * stride, v[L]);
+        if (L < Lev<S>::N) tc::tmem_ld4(taddr + L * stride, v[L]);
         else {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[L][c] = 0u;
+            for (int c = 0; c < 4; ++c) v[L][c] = 0u;
         }
     }
 }
@@ -309,12 +326,14 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 template <int S>
 struct RowCfg {
-    static constexpr int STAGES = S >= 4 ? 2 : (S == 3 ? 3 : 4);
     static constexpr int A_TILE = NP * BK * 2;                 // 8 KB
     static constexpr int B_TILE = NP * BK * 2;                 // up to 128 rows: 8 KB
     static constexpr int STAGE_BYTES = S * (A_TILE + B_TILE);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 2048;
-    static_assert(STAGES * STAGE_BYTES >= 128 * 64 * 16, "epilogue staging must fit");
+    static constexpr int STAGES_FIT = (200 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
+    // stages, then barriers, column tables and the reduction partials (< 6 KB), 1 KB alignment
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 8192;
+    static_assert(STAGES >= 2, "at least two pipeline stages");
 };
 
 __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_local, int ct)
@@ -335,6 +354,23 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_loca
     return false;
 }
 
+// Wait with a fixed spin limit and no early exit (draining copies after an error).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
+{
+    for (long long it = 0; it < tc::kWaitLimit; ++it)
+        if (tc::mbar_try_wait(bar, parity)) return;
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory"); }
+
+// Persistent row GEMM: one CTA per SM walks the tiles blockIdx.x, +gridDim.x, ... Roles:
+//   warp 0 (one lane): TMA producer over a ring of STAGES shared-memory stages that runs across
+//                      tiles, so the next tile's operands stream in during this tile's epilogue;
+//   warp 1 (one lane): MMA issuer; all 512 TMEM columns hold the four level accumulators of one
+//                      128 x bnc-complex tile, so it waits until the epilogue has read them;
+//   warps 2..9       : epilogue (lane quarter = warp % 4, column half = (warp - 2) / 4). Values
+//                      needed twice (a column exponent before slicing) are read from TMEM twice
+//                      instead of being staged in shared memory.
 template <int S, int MODE>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
     k_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -346,28 +382,29 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     uint8_t* stage_base = smem;
     uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
     uint64_t* empty = full + C::STAGES;
-    uint64_t* acc_full = empty + C::STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
-    int* colE = (int*)(tmem_slot + 4);   // 64 ints: column exponent keys
-    int* colEb = colE + 64;              // 64 ints: fixed-matrix column exponents
+    uint64_t* tfull = empty + C::STAGES;       // MMA -> epilogue: accumulators complete
+    uint64_t* tempty = tfull + 1;              // epilogue -> MMA: accumulators read
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+    int* stop = (int*)(tmem_slot + 1);
+    int* colE = (int*)(tmem_slot + 4);         // 64 column exponent keys
+    int* colEb = colE + 64;                    // 64 fixed-matrix column exponents
+    float4* red = (float4*)(colEb + 64);       // [4 lane quarters][64 columns] reduction partials
+    float2* lamf = (float2*)(red + 4 * 64);    // 64 lambda_q in FP32 (exponent estimates)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t tile = blockIdx.x;
-    const int ct = (int)(tile % args.ncol_tiles);
-    const int64_t rt = tile / args.ncol_tiles;
-    const int64_t row0 = rt * NP;
-    if (tile_skipped(args, row0, ct)) return;   // uniform over the CTA
-    unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
-    if (trc && threadIdx.x == 0) trc[0] = global_ns();
-    const int bnr = 2 * args.bnc;
+    const int bnc = args.bnc;
+    const int bnr = 2 * bnc;
     const uint32_t b_bytes_tile = (uint32_t)bnr * BK * 2;
+    const int64_t ntiles = args.num_tiles;
+    const int ncol = args.ncol_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(acc_full, 1);
+        tc::mbar_init(tfull, 1);
+        tc::mbar_init(tempty, 1);
         tc::fence_mbar_init();
         tc::tma_prefetch(&tmA);
         tc::tma_prefetch(&tmB);
@@ -376,316 +413,388 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         tc::tmem_alloc(tmem_slot, TMEM_COLS);
         tc::tmem_relinquish();
     }
-    if (threadIdx.x >= 64 && threadIdx.x < 128) {
-        colE[threadIdx.x - 64] = 0;
-        colEb[threadIdx.x - 64] = args.eb[ct * args.bnc + threadIdx.x - 64];
-    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    if (trc && threadIdx.x == 0) trc[1] = global_ns();
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
-        const int bc = ct * args.bnc;
-        for (int kc = 0; kc < args.kch; ++kc) {
-            const int st = kc % C::STAGES;
-            const uint32_t ph = (kc / C::STAGES) & 1;
-            if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) break;
-            uint8_t* sA = stage_base + st * C::STAGE_BYTES;
-            uint8_t* sB = sA + S * C::A_TILE;
-            tc::mbar_arrive_expect_tx(&full[st], S * (C::A_TILE + b_bytes_tile));
-            for (int s = 0; s < S; ++s)
-                tc::tma_load_2d(sA + s * C::A_TILE, &tmA, kc * BK, s * args.a_rows + (int)row0,
-                                &full[st]);
-            for (int t = 0; t < S; ++t) {
-                uint8_t* dst = sB + t * C::B_TILE;
-                tc::tma_load_2d(dst, &tmB, kc * BK, t * 512 + bc, &full[st]);
-                tc::tma_load_2d(dst + args.bnc * BK * 2, &tmB, kc * BK, t * 512 + 256 + bc,
-                                &full[st]);
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer: slice pairs (s, t), s + t < S, accumulated by level
-        const uint32_t idesc = tc::idesc_bf16_f32(128, bnr);
-        bool first[4] = {true, true, true, true};
-        for (int kc = 0; kc < args.kch; ++kc) {
-            const int st = kc % C::STAGES;
-            const uint32_t ph = (kc / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) break;
-            tc::fence_after_sync();
-            if (trc && kc == 0) trc[2] = global_ns();   // first stage landed
-            const uint32_t aBase = tc::smem_u32(stage_base + st * C::STAGE_BYTES);
-            const uint32_t bBase = aBase + S * C::A_TILE;
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-#pragma unroll
-                for (int t = 0; t < S - s; ++t) {
-                    const int L = s + t < 3 ? s + t : 3;
-#pragma unroll
-                    for (int ks = 0; ks < BK / 16; ++ks) {
-                        const uint64_t ad = tc::sdesc_sw64(aBase + s * C::A_TILE + ks * 32);
-                        const uint64_t bd = tc::sdesc_sw64(bBase + t * C::B_TILE + ks * 32);
-                        tc::mma_bf16(tmem + L * 128, ad, bd, idesc, first[L] ? 0u : 1u);
-                        first[L] = false;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            uint32_t it = 0;
+            bool alive = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+                const int ct = (int)(tile % ncol);
+                const int64_t row0 = tile / ncol * NP;
+                if (tile_skipped(args, row0, ct)) continue;
+                const int bc = ct * bnc;
+                for (int kc = 0; kc < args.kch; ++kc, ++it) {
+                    const int st = (int)(it % C::STAGES);
+                    const uint32_t ph = (it / C::STAGES) & 1;
+                    if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) {
+                        alive = false;
+                        break;
+                    }
+                    uint8_t* sA = stage_base + st * C::STAGE_BYTES;
+                    uint8_t* sB = sA + S * C::A_TILE;
+                    tc::mbar_arrive_expect_tx(&full[st], S * (C::A_TILE + b_bytes_tile));
+                    for (int s = 0; s < S; ++s)
+                        tc::tma_load_2d(sA + s * C::A_TILE, &tmA, kc * BK,
+                                        s * args.a_rows + (int)row0, &full[st]);
+                    for (int t = 0; t < S; ++t) {
+                        uint8_t* dst = sB + t * C::B_TILE;
+                        tc::tma_load_2d(dst, &tmB, kc * BK, t * 512 + bc, &full[st]);
+                        tc::tma_load_2d(dst + bnc * BK * 2, &tmB, kc * BK, t * 512 + 256 + bc,
+                                        &full[st]);
                     }
                 }
-            tc::mma_commit(&empty[st]);
-        }
-        tc::mma_commit(acc_full);
-    } else if (warp >= 2) {
-        // ---------------- epilogue: 8 warps, lane quarter = warp % 4, column half = (warp-2)/4
-        const int q4 = warp % 4;
-        const int half = (warp - 2) / 4;
-        const int rl = q4 * 32 + lane;                      // local row within the tile
-        const int64_t o = row0 + rl;                        // local row of the launch
-        const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
-        const bool ok = tc::mbar_wait(acc_full, 0, args.err, kErrTimeout);
-        tc::fence_after_sync();
-        if (trc && threadIdx.x == 64) trc[3] = global_ns();   // accumulators complete
-        const int bnc = args.bnc;
-        const int cols = bnc / 2;
-        const int cbeg = half * cols;
-        const int qbase = ct * bnc;
-        const int ea = args.ea[o >> args.ea_shift];
-        const int64_t outer = o / args.R;
-        const int64_t rr = o % args.R;
-        const int64_t rblk = rr / NP;
-        const int64_t rperq = args.R / NP;
-        const int N = args.N, n = args.n;
-
-        // row digits: the first rp are p's (must be in order and < n), then a's (< n)
-        int dg[8];
-        row_digits(rr, N - 1, dg);
-        bool row_ok = true;
-        int firstp = NP;
-        if (args.digits) {
-#pragma unroll
-            for (int m = 0; m < 7; ++m) {
-                if (m < N - 1) {
-                    row_ok &= dg[m] < n;
-                    if (m >= 1 && m < args.rp) row_ok &= dg[m - 1] <= dg[m];
-                }
             }
-            if (args.rp >= 1) firstp = dg[0];
-        }
-
-        // EPI_DIVIDE / EPI_SLAB: sigma of the row p's minus lambda_i, multiplicity base and the
-        // length of the first run of equal p's
-        double2 sigma = make_double2(0, 0);
-        double mult_base = 1.0;
-        int run1 = 1;
-        if (MODE == EPI_DIVIDE || MODE == EPI_SLAB) {
-            const int np_row = args.rp;
-            if (row_ok) {
-#pragma unroll
-                for (int m = 0; m < 7; ++m)
-                    if (m < np_row) sigma = cadd(sigma, args.lam[dg[m]]);
-                sigma = csub(sigma, args.lam[args.i0 + (int)outer]);
+            if (!alive) {
+                // after an error: let the copies already issued land before the CTA exits
+                const uint32_t first = it > (uint32_t)C::STAGES ? it - C::STAGES : 0u;
+                for (uint32_t j = first; j < it; ++j)
+                    mbar_drain(&full[j % C::STAGES], (j / C::STAGES) & 1);
             }
-            double denom = 1.0;
-            int run = 1;
-            bool first_run = true;
-#pragma unroll
-            for (int m = 1; m < 8; ++m) {
-                if (m > np_row) break;
-                if (m < np_row && dg[m] == dg[m - 1]) {
-                    ++run;
-                } else {
-                    if (first_run) run1 = run;
-                    first_run = false;
-                    for (int t = 2; t <= run; ++t) denom *= t;
-                    run = 1;
-                }
-            }
-            double nf = 1.0;
-            for (int t = 2; t <= N; ++t) nf *= t;
-            mult_base = nf / denom;
         }
-        long long* vbuf = (long long*)stage_base;     // [64 cols][128 rows][2] (pipeline drained)
-        double2* hbuf = (double2*)stage_base;         // same storage, FP64 quotients
-        float4* gbuf = (float4*)stage_base;           // same storage, double-float products
-
-        if (ok) {
-            // pass 1: recombine, exponents (FP64 quotients / weighted products), stage in smem
-            for (int c8 = cbeg; c8 < cbeg + cols; c8 += 8) {
-                uint32_t rv[4][8], iv[4][8];
-                load_levels<S>(trow + c8, 128, rv);
-                load_levels<S>(trow + bnc + c8, 128, iv);
-                tc::tmem_wait_ld();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: slice pairs (s, t), s + t < S, accumulated by level
+            const uint32_t idesc = tc::idesc_bf16_f32(128, bnr);
+            uint32_t it = 0, t = 0;
+            bool alive = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+                const int ct = (int)(tile % ncol);
+                const int64_t row0 = tile / ncol * NP;
+                if (tile_skipped(args, row0, ct)) continue;
+                if (!tc::mbar_wait(tempty, (t & 1) ^ 1, args.err, kErrTimeout)) break;
+                tc::fence_after_sync();
+                bool first[4] = {true, true, true, true};
+                for (int kc = 0; kc < args.kch; ++kc, ++it) {
+                    const int st = (int)(it % C::STAGES);
+                    const uint32_t ph = (it / C::STAGES) & 1;
+                    if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) {
+                        alive = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t aBase = tc::smem_u32(stage_base + st * C::STAGE_BYTES);
+                    const uint32_t bBase = aBase + S * C::A_TILE;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int cl = c8 + c;
-                    const int qc = qbase + cl;
-                    const int eb = colEb[cl];
-                    const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
-                    const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                    const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
-                    unsigned key = 0;
-                    if (MODE == EPI_SLICE || MODE == EPI_F64T) {
-                        vbuf[((size_t)cl * NP + rl) * 2 + 0] = Vr;
-                        vbuf[((size_t)cl * NP + rl) * 2 + 1] = Vi;
-                        const int bl = max(bitlen64(Vr), bitlen64(Vi));
-                        if (valid && bl) key = (unsigned)(bl + ea + eb - VEXP + 8192);
-                    } else if (MODE == EPI_REDUCE) {
-                        // G[c'][k] psi_{p_{N-1} k} in double-float (p_{N-1} = innermost digit)
-                        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (valid && (Vr | Vi)) {
-                            const int sc = ea + eb - VEXP;
-                            const dfl gr = df_from_i64(Vr, sc), gi = df_from_i64(Vi, sc);
-                            int pin = 0;   // innermost digit p_{N-1}, selected with static indices
+                    for (int s = 0; s < S; ++s)
 #pragma unroll
-                            for (int m = 0; m < 7; ++m)
-                                if (m == N - 2) pin = dg[m];
-                            const float4 w = args.psi_df[(int64_t)pin * n + qc];
-                            const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
-                            const dfl pr = df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi)));
-                            const dfl pi = df_add(df_mul(gr, wi), df_mul(gi, wr));
-                            g = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
-                        }
-                        gbuf[(size_t)cl * NP + rl] = g;
-                    } else {
-                        double2 h = make_double2(0, 0);
-                        if (valid && (Vr | Vi)) {
-                            const double mult = (qc == firstp) ? mult_base / (run1 + 1) : mult_base;
-                            const double sc = pow2d(ea + eb - VEXP) * args.invfact *
-                                              (MODE == EPI_DIVIDE ? mult : 1.0);
-                            h = make_double2((double)Vr * sc, (double)Vi * sc);
-                            if (args.divide) {
-                                // h / D = h conj(D) / |D|^2 (FP64), D clamped per Alg. 2 step 9
-                                double2 D = cadd(sigma, args.lam[qc]);
-                                double m2 = fma(D.x, D.x, D.y * D.y);
-                                if (m2 < args.eps * args.eps) {
-                                    D = make_double2(args.eps, 0.0);
-                                    m2 = args.eps * args.eps;
-                                }
-                                const double r = __drcp_rn(m2);
-                                h = make_double2(fma(h.x, D.x, h.y * D.y) * r,
-                                                 fma(h.y, D.x, -h.x * D.y) * r);
+                        for (int u = 0; u < S - s; ++u) {
+                            const int L = s + u < 3 ? s + u : 3;
+#pragma unroll
+                            for (int ks = 0; ks < BK / 16; ++ks) {
+                                const uint64_t ad = tc::sdesc_sw64(aBase + s * C::A_TILE + ks * 32);
+                                const uint64_t bd = tc::sdesc_sw64(bBase + u * C::B_TILE + ks * 32);
+                                tc::mma_bf16(tmem + L * 128, ad, bd, idesc, first[L] ? 0u : 1u);
+                                first[L] = false;
                             }
                         }
-                        hbuf[(size_t)cl * NP + rl] = h;
-                        const double mm = fmax(fabs(h.x), fabs(h.y));
-                        if (mm > 0.0) {
-                            int e;
-                            frexp(mm, &e);
-                            key = (unsigned)(e + 8192);
-                        }
-                    }
-                    if (MODE != EPI_REDUCE) {
-                        const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
-                        if (lane == 0 && wmax) atomicMax(&colE[cl], (int)wmax);
-                    }
+                    tc::mma_commit(&empty[st]);
                 }
+                if (!alive) break;
+                tc::mma_commit(tfull);
+                ++t;
             }
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
-        if (trc && threadIdx.x == 64) trc[4] = global_ns();   // pass 1 done
-        if (MODE == EPI_REDUCE) {
-            // pass 2: column sums over the 128 rows (four parts per column), then the prefix
-            // weight prod_{m<=N-2} psi_{p_m k} and -sum into Psi_N[i][k]
-            const int t = (warp - 2) * 32 + lane;      // 0..255
-            const int cl = t % 64, part = t / 64;      // 4 parts of 32 rows
-            dfl sr = {0.f, 0.f}, si = {0.f, 0.f};
-            if (ok)
-                for (int r = part * 32; r < part * 32 + 32; ++r) {
-                    const float4 g = gbuf[(size_t)cl * NP + r];
-                    sr = df_add(sr, dfl{g.x, g.y});
-                    si = df_add(si, dfl{g.z, g.w});
-                }
-            asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
-            float4* red = gbuf;                        // reuse: [4 parts][64 cols]
-            red[part * 64 + cl] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
-            asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
-            const int qc = qbase + cl;
-            if (ok && part == 0 && cl < bnc && qc < n) {   // the tile holds bnc columns
-                dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
-                for (int pp = 0; pp < 4; ++pp) {
-                    const float4 g = red[pp * 64 + cl];
-                    ar = df_add(ar, dfl{g.x, g.y});
-                    ai = df_add(ai, dfl{g.z, g.w});
-                }
-                if (ar.hi != 0.f || ai.hi != 0.f) {
-                    // the tile shares (i, p_1..p_{N-2}): recover them from the tile's first row
-                    int d0[8];
-                    row_digits((row0 % args.R), N - 1, d0);
-                    double2 w = make_double2(1.0, 0.0);
-#pragma unroll
-                    for (int m = 0; m < 6; ++m)
-                        if (m < N - 2) w = cmul(w, args.V[(int64_t)d0[m] * n + qc]);
-                    const int i = args.i0 + (int)(row0 / args.R);
-                    const double2 v = cmul(make_double2(df_to_d(ar), df_to_d(ai)), w);
-                    atomicAdd(&args.out_f64[(int64_t)i * n + qc].x, -v.x);
-                    atomicAdd(&args.out_f64[(int64_t)i * n + qc].y, -v.y);
+    } else {
+        // ---------------- epilogue
+        const int et = threadIdx.x - 64;                    // 0 .. 32 * EPI_WARPS - 1
+        const int q4 = warp % 4;                            // TMEM lane quarter of this warp
+        const int grp = (warp - 2) / 4;                     // column group (EPI_WARPS / 4 groups)
+        const int rl = q4 * 32 + lane;                      // local row within the tile
+        const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
+        const int cols = bnc / (EPI_WARPS / 4);             // >= 4 for bnc >= 16
+        const int cbeg = grp * cols;
+        const int N = args.N, n = args.n;
+        uint32_t t = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int ct = (int)(tile % ncol);
+            const int64_t row0 = tile / ncol * NP;
+            if (tile_skipped(args, row0, ct)) continue;
+            unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
+            if (et < 64) {
+                colE[et] = 0;
+                colEb[et] = args.eb[ct * bnc + et];
+                if (MODE == EPI_DIVIDE) {
+                    const int q = ct * bnc + et;
+                    lamf[et] = q < n ? make_float2((float)args.lam[q].x, (float)args.lam[q].y)
+                                     : make_float2(0.f, 0.f);
                 }
             }
-        } else if (ok) {
-            // pass 2: outputs
-            for (int cl = cbeg; cl < cbeg + cols; ++cl) {
+            if (et == 0) *stop = *(volatile int*)args.err;
+            epi_sync();
+            if (*stop) break;                                // uniform over the epilogue warps
+            if (trc && et == 0) trc[0] = global_ns();
+            const bool ok = tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout);
+            tc::fence_after_sync();
+            if (trc && et == 0) trc[1] = global_ns();         // accumulators complete
+            const int qbase = ct * bnc;
+            const int64_t o = row0 + rl;                      // local row of the launch
+            const int ea = args.ea[o >> args.ea_shift];
+            const int64_t outer = o / args.R;
+            const int64_t rr = o % args.R;
+            const int64_t rblk = rr / NP;
+            const int64_t rperq = args.R / NP;
+
+            // row digits: the first rp are p's (must be in order and < n), then a's (< n)
+            int dg[8];
+            row_digits(rr, N - 1, dg);
+            bool row_ok = true;
+            int firstp = NP;
+            if (args.digits) {
+#pragma unroll
+                for (int m = 0; m < 7; ++m) {
+                    if (m < N - 1) {
+                        row_ok &= dg[m] < n;
+                        if (m >= 1 && m < args.rp) row_ok &= dg[m - 1] <= dg[m];
+                    }
+                }
+                if (args.rp >= 1) firstp = dg[0];
+            }
+
+            // EPI_DIVIDE / EPI_SLAB: sigma of the row p's minus lambda_i, multiplicity base and
+            // the length of the first run of equal p's
+            double2 sigma = make_double2(0, 0);
+            double mult_base = 1.0;
+            int run1 = 1;
+            if (MODE == EPI_DIVIDE || MODE == EPI_SLAB) {
+                const int np_row = args.rp;
+                if (row_ok) {
+#pragma unroll
+                    for (int m = 0; m < 7; ++m)
+                        if (m < np_row) sigma = cadd(sigma, args.lam[dg[m]]);
+                    sigma = csub(sigma, args.lam[args.i0 + (int)outer]);
+                }
+                double denom = 1.0;
+                int run = 1;
+                bool first_run = true;
+#pragma unroll
+                for (int m = 1; m < 8; ++m) {
+                    if (m > np_row) break;
+                    if (m < np_row && dg[m] == dg[m - 1]) {
+                        ++run;
+                    } else {
+                        if (first_run) run1 = run;
+                        first_run = false;
+                        for (int u = 2; u <= run; ++u) denom *= u;
+                        run = 1;
+                    }
+                }
+                double nf = 1.0;
+                for (int u = 2; u <= N; ++u) nf *= u;
+                mult_base = nf / denom;
+            }
+
+            // h of one element (EPI_DIVIDE / EPI_SLAB): V * 2^(ea+eb-VEXP) / N! (times the
+            // multiplicity for the reduction), divided by the clamped denominator in FP64
+            auto quotient = [&](long long Vr, long long Vi, int eb, int qc) -> double2 {
+                const double mult = (qc == firstp) ? mult_base / (run1 + 1) : mult_base;
+                const double sc = pow2d(ea + eb - VEXP) * args.invfact *
+                                  (MODE == EPI_DIVIDE ? mult : 1.0);
+                double2 h = make_double2((double)Vr * sc, (double)Vi * sc);
+                if (args.divide) {
+                    // h / D = h conj(D) / |D|^2, D clamped per Alg. 2 step 9
+                    double2 D = cadd(sigma, args.lam[qc]);
+                    double m2 = fma(D.x, D.x, D.y * D.y);
+                    if (m2 < args.eps * args.eps) {
+                        D = make_double2(args.eps, 0.0);
+                        m2 = args.eps * args.eps;
+                    }
+                    const double r = __drcp_rn(m2);
+                    h = make_double2(fma(h.x, D.x, h.y * D.y) * r, fma(h.y, D.x, -h.x * D.y) * r);
+                }
+                return h;
+            };
+
+            if (MODE == EPI_SLICE || MODE == EPI_DIVIDE) {
+                // pass 1: column exponents (max over the tile's valid rows). For the quotients an
+                // FP32 upper bound of |h| = |V| 2^(ea+eb-VEXP) f / |D| with a lower bound of the
+                // clamped |D| (FP32 error of sigma + lambda_q bounded by 4 ulp of its terms).
+                const float2 sf = make_float2((float)sigma.x, (float)sigma.y);
+                const float fmb = (float)(args.invfact * mult_base);
+                if (ok) {
+                    for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
+                        uint32_t rv[4][4], iv[4][4];
+                        load_levels<S>(trow + c4, 128, rv);
+                        load_levels<S>(trow + bnc + c4, 128, iv);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int cl = c4 + c;
+                            const int qc = qbase + cl;
+                            const int eb = colEb[cl];
+                            const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
+                            const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
+                            const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
+                            unsigned key = 0;
+                            if (MODE == EPI_SLICE) {
+                                const int bl = max(bitlen64(Vr), bitlen64(Vi));
+                                if (valid && bl) key = (unsigned)(bl + ea + eb - VEXP + 8192);
+                            } else if (valid && (Vr | Vi)) {
+                                float lb = 1.0f;
+                                if (args.divide) {
+                                    const float2 lq = lamf[cl];
+                                    const float dx = sf.x + lq.x, dy = sf.y + lq.y;
+                                    const float del = 2.4e-7f * (fabsf(sf.x) + fabsf(sf.y) +
+                                                                fabsf(lq.x) + fabsf(lq.y));
+                                    lb = fmaxf(sqrtf(fmaf(dx, dx, dy * dy)) - del, (float)args.eps);
+                                }
+                                // |V| from 22-bit pieces (32-bit conversions only)
+                                const float fr = fmaf((float)(int)(Vr >> 22), 4194304.0f,
+                                                      (float)(int)(Vr & 0x3FFFFF));
+                                const float fi = fmaf((float)(int)(Vi >> 22), 4194304.0f,
+                                                      (float)(int)(Vi & 0x3FFFFF));
+                                const float fm = qc == firstp ? fmb / (float)(run1 + 1) : fmb;
+                                const float hm = sqrtf(fmaf(fr, fr, fi * fi)) * fm / lb *
+                                                 (1.0f + 0.0009765625f);
+                                int e;
+                                frexpf(hm, &e);
+                                key = (unsigned)(e + ea + eb - VEXP + 8192);
+                            }
+                            const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+                            if (lane == 0 && wmax) atomicMax(&colE[cl], (int)wmax);
+                        }
+                    }
+                }
+                epi_sync();
+                if (trc && et == 0) trc[2] = global_ns();
+            }
+
+            if (ok) {
+                // pass 2 (or the only pass): outputs
+                for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
+                    uint32_t rv[4][4], iv[4][4];
+                    load_levels<S>(trow + c4, 128, rv);
+                    load_levels<S>(trow + bnc + c4, 128, iv);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int cl = c4 + c;
+                        const int qc = qbase + cl;
+                        const int eb = colEb[cl];
+                        const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
+                        const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
+                        if (MODE == EPI_REDUCE) {
+                            // G[c'][k] psi_{p_{N-1} k} (double-float), summed over the warp's
+                            // 32 rows by shuffles; lane 0 keeps the warp's partial
+                            dfl pr = {0.f, 0.f}, pi = {0.f, 0.f};
+                            if (row_ok && qc < n && (Vr | Vi)) {
+                                const int sc = ea + eb - VEXP;
+                                const dfl gr = df_from_i64(Vr, sc), gi = df_from_i64(Vi, sc);
+                                int pin = 0;   // innermost digit p_{N-1} (static indices)
+#pragma unroll
+                                for (int m = 0; m < 7; ++m)
+                                    if (m == N - 2) pin = dg[m];
+                                const float4 w = args.psi_df[(int64_t)pin * n + qc];
+                                const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
+                                pr = df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi)));
+                                pi = df_add(df_mul(gr, wi), df_mul(gi, wr));
+                            }
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1) {
+                                const dfl orr = {__shfl_xor_sync(0xffffffffu, pr.hi, off),
+                                                 __shfl_xor_sync(0xffffffffu, pr.lo, off)};
+                                const dfl oi = {__shfl_xor_sync(0xffffffffu, pi.hi, off),
+                                                __shfl_xor_sync(0xffffffffu, pi.lo, off)};
+                                pr = df_add(pr, orr);
+                                pi = df_add(pi, oi);
+                            }
+                            if (lane == 0) red[q4 * 64 + cl] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+                            continue;
+                        }
+                        if (qc >= args.npc) continue;
+                        if (MODE == EPI_F64T) {
+                            if (qc < n) {
+                                const double sc = pow2d(ea + eb - VEXP);
+                                args.out_f64[(int64_t)qc * args.ld_f64 + o] =
+                                    make_double2((double)Vr * sc, (double)Vi * sc);
+                            }
+                            continue;
+                        }
+                        const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
+                        if (MODE == EPI_SLAB) {
+                            // store h^i_{pre, q} when the multiset (q, row p's) minus pre is {extra}
+                            if (!valid || !(Vr | Vi)) continue;
+                            const double2 h = quotient(Vr, Vi, eb, qc);
+                            int tt[8];
+                            tt[0] = qc;
+                            for (int m = 0; m < args.rp; ++m) tt[m + 1] = dg[m];
+                            int used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                            int matched = 0, extra = -1, nextra = 0;
+                            for (int a = 0; a < N; ++a) {
+                                bool hit = false;
+                                for (int b = 0; b < N - 1 && !hit; ++b)
+                                    if (!used[b] && args.pre[b] == tt[a]) { used[b] = 1; hit = true; }
+                                if (hit) ++matched;
+                                else { extra = tt[a]; ++nextra; }
+                            }
+                            if (matched == N - 1 && nextra == 1)
+                                args.out_f64[(int64_t)(args.i0 + outer) * n + extra] = h;
+                            continue;
+                        }
+                        if (args.colmask && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
+                        const int64_t rowp = (outer * args.npc + qc) * rperq + rblk;
+                        const int key = colE[cl];
+                        const int E = key ? key - 8192 : EXP_NONE;
+                        uint32_t w[S];
+                        if (key == 0 || !valid) {
+#pragma unroll
+                            for (int s = 0; s < S; ++s) w[s] = 0u;
+                        } else if (MODE == EPI_SLICE) {
+                            const int sh = ea + eb - VEXP - E + 7 + 8 * (S - 1);
+                            digit_pairs<S>(shift_round(Vr, sh), shift_round(Vi, sh), w);
+                        } else {
+                            const double2 h = quotient(Vr, Vi, eb, qc);
+                            const double sc = pow2d(7 + 8 * (S - 1) - E);
+                            digit_pairs<S>(__double2ll_rn(h.x * sc), __double2ll_rn(h.y * sc), w);
+                        }
+                        uint32_t* dst = reinterpret_cast<uint32_t*>(args.out_planes) + rowp * (KP / 2) + rl;
+#pragma unroll
+                        for (int s = 0; s < S; ++s) dst[s * (args.out_plane_stride / 2)] = w[s];
+                        if (rl == 0) args.out_exp[rowp] = E;
+                    }
+                }
+            }
+            if (MODE == EPI_REDUCE) {
+                // the four lane quarters' partials of every column, the prefix weight
+                // prod_{m<=N-2} psi_{p_m k}, and -sum into Psi_N[i][k]
+                epi_sync();
+                const int cl = et;
                 const int qc = qbase + cl;
-                if (qc >= args.npc) continue;
-                const int key = colE[cl];
-                if (MODE == EPI_F64T) {
-                    if (qc < n) {
-                        const long long Vr = vbuf[((size_t)cl * NP + rl) * 2 + 0];
-                        const long long Vi = vbuf[((size_t)cl * NP + rl) * 2 + 1];
-                        const double sc = pow2d(ea + colEb[cl] - VEXP);
-                        args.out_f64[(int64_t)qc * args.ld_f64 + o] =
-                            make_double2((double)Vr * sc, (double)Vi * sc);
+                if (ok && cl < bnc && qc < n) {
+                    dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
+                    for (int pp = 0; pp < 4; ++pp) {
+                        const float4 g = red[pp * 64 + cl];
+                        ar = df_add(ar, dfl{g.x, g.y});
+                        ai = df_add(ai, dfl{g.z, g.w});
                     }
-                    continue;
-                }
-                if (MODE == EPI_SLAB) {
-                    // store h^i_{pre, q} when the multiset (q, row p's) minus pre is {extra}
-                    const double2 h = hbuf[(size_t)cl * NP + rl];
-                    const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
-                    if (!valid) continue;
-                    int t[8];
-                    t[0] = qc;
-                    for (int m = 0; m < args.rp; ++m) t[m + 1] = dg[m];
-                    int used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    int matched = 0, extra = -1, nextra = 0;
-                    for (int a = 0; a < N; ++a) {
-                        bool hit = false;
-                        for (int b = 0; b < N - 1 && !hit; ++b)
-                            if (!used[b] && args.pre[b] == t[a]) { used[b] = 1; hit = true; }
-                        if (hit) ++matched;
-                        else { extra = t[a]; ++nextra; }
+                    if (ar.hi != 0.f || ai.hi != 0.f) {
+                        // the tile shares (i, p_1..p_{N-2}): recover them from its first row
+                        int d0[8];
+                        row_digits((row0 % args.R), N - 1, d0);
+                        double2 wgt = make_double2(1.0, 0.0);
+#pragma unroll
+                        for (int m = 0; m < 6; ++m)
+                            if (m < N - 2) wgt = cmul(wgt, args.V[(int64_t)d0[m] * n + qc]);
+                        const int i = args.i0 + (int)(row0 / args.R);
+                        const double2 v = cmul(make_double2(df_to_d(ar), df_to_d(ai)), wgt);
+                        atomicAdd(&args.out_f64[(int64_t)i * n + qc].x, -v.x);
+                        atomicAdd(&args.out_f64[(int64_t)i * n + qc].y, -v.y);
                     }
-                    if (matched == N - 1 && nextra == 1)
-                        args.out_f64[(int64_t)(args.i0 + outer) * n + extra] = h;
-                    continue;
                 }
-                if (args.colmask && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
-                const int64_t rowp = (outer * args.npc + qc) * rperq + rblk;
-                const int E = key ? key - 8192 : EXP_NONE;
-                uint32_t w[S];
-                if (key == 0) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s) w[s] = 0u;
-                } else if (MODE == EPI_SLICE) {
-                    const int sh = ea + colEb[cl] - VEXP - E + 7 + 8 * (S - 1);
-                    const long long Vr = vbuf[((size_t)cl * NP + rl) * 2 + 0];
-                    const long long Vi = vbuf[((size_t)cl * NP + rl) * 2 + 1];
-                    const bool valid = row_ok && qc < n;
-                    digit_pairs<S>(valid ? shift_round(Vr, sh) : 0, valid ? shift_round(Vi, sh) : 0,
-                                   w);
-                } else {
-                    const double2 h = hbuf[(size_t)cl * NP + rl];
-                    const double sc = pow2d(7 + 8 * (S - 1) - E);
-                    digit_pairs<S>(__double2ll_rn(h.x * sc), __double2ll_rn(h.y * sc), w);
-                }
-                uint32_t* dst = reinterpret_cast<uint32_t*>(args.out_planes) + rowp * (KP / 2) + rl;
-#pragma unroll
-                for (int s = 0; s < S; ++s) dst[s * (args.out_plane_stride / 2)] = w[s];
-                if (rl == 0) args.out_exp[rowp] = E;
             }
+            tc::fence_before_sync();
+            epi_sync();
+            if (trc && et == 0) trc[3] = global_ns();
+            if (et == 0) tc::mbar_arrive(tempty);
+            ++t;
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (trc && threadIdx.x == 0) trc[5] = global_ns();
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, TMEM_COLS);
@@ -1042,29 +1151,38 @@ void split_prepare_tensor(Plan& p, int N)
 // phase times (%globaltimer) and prints the median phase durations to stderr.
 static void trace_report(const char* name, const std::vector<unsigned long long>& t, int64_t tiles)
 {
-    std::vector<double> d[5];
+    std::vector<double> d[3];
     unsigned long long t0 = ~0ull, t1 = 0;
     int64_t ran = 0;
     for (int64_t k = 0; k < tiles; ++k) {
         const unsigned long long* r = &t[k * 6];
-        if (!r[0] || !r[5]) continue;
+        if (!r[0] || !r[3]) continue;
         ++ran;
         t0 = std::min(t0, r[0]);
-        t1 = std::max(t1, r[5]);
-        d[0].push_back((double)(r[1] - r[0]));   // setup (barriers, TMEM alloc)
-        d[1].push_back((double)(r[2] - r[1]));   // first stage fill
-        d[2].push_back((double)(r[3] - r[2]));   // MMA from first stage to completion
-        d[3].push_back((double)(r[4] - r[3]));   // epilogue pass 1
-        d[4].push_back((double)(r[5] - r[4]));   // epilogue pass 2 + teardown
+        t1 = std::max(t1, r[3]);
+        d[0].push_back((double)(r[1] - r[0]));                   // epilogue waiting for the MMA
+        d[1].push_back(r[2] ? (double)(r[2] - r[1]) : 0.0);      // column-exponent pass
+        d[2].push_back((double)(r[3] - (r[2] ? r[2] : r[1])));   // output pass
     }
     auto med = [](std::vector<double>& v) {
         if (v.empty()) return 0.0;
         std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
         return v[v.size() / 2] * 1e-3;
     };
-    fprintf(stderr, "[trace] %s tiles %lld ran %lld span %.1f us | median us: setup %.2f fill %.2f "
-            "mma %.2f epi1 %.2f epi2 %.2f\n", name, (long long)tiles, (long long)ran,
-            (t1 > t0 ? (t1 - t0) : 0) * 1e-3, med(d[0]), med(d[1]), med(d[2]), med(d[3]), med(d[4]));
+    fprintf(stderr, "[trace] %s tiles %lld ran %lld span %.1f us | median us: wait-mma %.2f "
+            "pass1 %.2f pass2 %.2f\n", name, (long long)tiles, (long long)ran,
+            (t1 > t0 ? (t1 - t0) : 0) * 1e-3, med(d[0]), med(d[1]), med(d[2]));
+}
+
+static int sm_count()
+{
+    static int count = 0;
+    if (!count) {
+        int dev = 0;
+        NPF_CUDA(cudaGetDevice(&dev));
+        NPF_CUDA(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return count;
 }
 
 template <int S, int MODE>
@@ -1080,7 +1198,12 @@ static void launch_rows(Plan& p, const char* name, const CUtensorMap& tA, const 
     }
     {
         LaunchScope ls(&p.prof, name, p.stream);
-        k_rows<S, MODE><<<(unsigned)a.num_tiles, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+        // persistent: one CTA per SM (the shared memory allows one), tiles strided over CTAs
+        // an odd stride keeps each CTA from seeing only one column tile (the column tiles of a
+        // row tile differ in cost under the sorted-tuple masks)
+        int64_t grid = std::min<int64_t>(a.num_tiles, sm_count());
+        if (grid > 1 && a.ncol_tiles > 1 && grid % 2 == 0) grid -= 1;
+        k_rows<S, MODE><<<(unsigned)std::max<int64_t>(grid, 1), ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
         NPF_CUDA(cudaGetLastError());
     }
     if (tracing) {
