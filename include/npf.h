@@ -74,10 +74,17 @@ enum npf_option {
                                sum_p C^i_p prod_m psi_{p_m k} = (1/N!) sum_j psi_ij A^j_{k..k}. */
     NPF_OPT_MEM_BUDGET = 5, /* bytes of device memory for intermediates; 0 = 80% of free memory. */
     NPF_OPT_PROFILE = 6,    /* 1: time each kernel launch with CUDA events (npf_get_profile). */
-    NPF_OPT_TILE_N = 7      /* complex columns per tensor-core tile: 16, 32 or 64 (default 64), or
+    NPF_OPT_TILE_N = 7,     /* complex columns per tensor-core tile: 16, 32 or 64 (default 64), or
                                0 = autotuned: the first term of each (n, order, precision,
                                slices, divide) times every width on the plan's own work and the
                                fastest is kept for the process (npf_tuned_tile). */
+    NPF_OPT_FP64_QUOTIENT = 8 /* tensor-core forms, Alg. 2 steps 5-11: 1 = form h = C / D with
+                               native FP64 arithmetic; 0 (default) = the denominator
+                               D = lambda_p1 + .. + lambda_pN - lambda_i exactly from FP64 inputs
+                               (error-free float transformations, exact under cancellation) and
+                               the quotient in double-float arithmetic (relative error ~2^-45),
+                               about 5x faster on this GPU, whose FP64 rate is ~1/900 of its
+                               tensor rate. Both are rounded to the same 6 x 8-bit slices next. */
 };
 
 /* Arithmetic of the dense contraction. The denominators, the divide, the Psi_N sums and the

@@ -176,6 +176,57 @@ __device__ __forceinline__ dfl df_from_i64(long long V, int sc)
     return {ldexpf(r.hi, sc), ldexpf(r.lo, sc)};
 }
 __device__ __forceinline__ double df_to_d(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl to_dfl(double x)
+{
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+
+// A double as the exact sum of three floats (24 + 24 + 5 significant bits).
+struct tfl { float a, b, c; };
+__device__ __forceinline__ tfl to_tfl(double x)
+{
+    const float a = (float)x;
+    const double r = x - (double)a;               // exact
+    const float b = (float)r;
+    return {a, b, (float)(r - (double)b)};        // exact
+}
+// s + l as a double-float for exact triple-float terms: the leading pieces are added with
+// error-free transformations, so the result keeps ~2^-48 relative accuracy however much they
+// cancel (near-resonant denominators).
+__device__ __forceinline__ dfl tfl_sum(const tfl& s, const tfl& l)
+{
+    const dfl A = two_sum(s.a, l.a);
+    const dfl B = two_sum(s.b, l.b);
+    const dfl X = two_sum(A.hi, B.hi);
+    const float y = (A.lo + B.lo) + ((s.c + l.c) + X.lo);
+    return two_sum(X.hi, y);
+}
+// L0 + L1 + L2 + L3 (one accumulator element, units of 2^30 in V) as a double-float.
+__device__ __forceinline__ dfl level_sum_df(uint32_t l0, uint32_t l1, uint32_t l2, uint32_t l3)
+{
+    const dfl t1 = two_sum(__uint_as_float(l0), __uint_as_float(l1));
+    const dfl t2 = two_sum(t1.hi, __uint_as_float(l2));
+    const dfl t3 = two_sum(t2.hi, __uint_as_float(l3));
+    return two_sum(t3.hi, (t1.lo + t2.lo) + t3.lo);
+}
+// round(x.hi + x.lo) for |x| < 2^47 with 32-bit conversions (off by at most one unit).
+__device__ __forceinline__ long long df_round_i64(dfl x)
+{
+    const int t = __float2int_rz(x.hi * 5.9604644775390625e-08f);          // 2^-24
+    const float rem = fmaf((float)t, -16777216.0f, x.hi);                   // exact
+    return ((long long)t << 24) + __float2int_rn(rem + x.lo);
+}
+
+// Per-row values of the quotient epilogues.
+struct RowInfo {
+    double2 sigma;        // sum of the row's p eigenvalues minus lambda_i
+    double mult_base;     // N! / prod(run lengths)!
+    tfl sr, si;           // sigma as exact triple-floats
+    dfl f_row, f_first;   // mult_base / N! (and with the first run one longer) as double-floats
+    int run1;
+    int pad;
+};
 
 // Recombined accumulator of one output element: V (units 2^-30 of the L0 integer grid).
 __device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t l2, uint32_t l3)
@@ -191,6 +242,20 @@ __device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t 
     const long long a3 = ((long long)h3 << 20) + r3;
     return (a0 << 30) + (a1 << 22) + (a2 << 14) + a3;
 }
+
+// Upper bound of |V| 2^-30 = |L0 + L1 + L2 + L3| + (rounding of L3 to the V grid, 2^-31): the
+// FP32 sum plus 2^-21 of the magnitudes (three roundings of at most 2^-24 each, and the rounding
+// of the bound itself) plus 2^-30.
+__device__ __forceinline__ float level_bound(uint32_t l0, uint32_t l1, uint32_t l2, uint32_t l3)
+{
+    const float a = __uint_as_float(l0), b = __uint_as_float(l1);
+    const float c = __uint_as_float(l2), d = __uint_as_float(l3);
+    const float s = ((a + b) + c) + d;
+    const float m = (fabsf(a) + fabsf(b)) + (fabsf(c) + fabsf(d));
+    return fmaf(m, 4.76837158203125e-07f, fabsf(s) + 9.313225746154785e-10f);   // 2^-21, 2^-30
+}
+// e with x < 2^e <= 2x for a positive normal float x (the frexp exponent)
+__device__ __forceinline__ int f32_exponent(float x) { return ((__float_as_int(x) >> 23) & 255) - 126; }
 
 // Number of TMEM level accumulators used by S slices (levels s + t < S, capped at 3).
 template <int S>
@@ -312,6 +377,8 @@ struct RowArgs {
     int i0;
     double invfact, eps;
     int divide;
+    int fp64_quotient;   // EPI_DIVIDE: native FP64 quotient instead of the double-float one
+    float eps2f;         // eps^2 in FP32 (clamp test of the double-float quotient)
     int pre[8];          // EPI_SLAB: the requested prefix (N-1 indices)
     int* err;
     unsigned long long* trace;   // optional per-CTA phase timestamps [tile][6] (nullptr: off)
@@ -331,8 +398,9 @@ struct RowCfg {
     static constexpr int STAGE_BYTES = S * (A_TILE + B_TILE);
     static constexpr int STAGES_FIT = (200 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
-    // stages, then barriers, column tables and the reduction partials (< 6 KB), 1 KB alignment
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 8192;
+    // stages, then barriers, column tables, reduction partials and row tables (< 17 KB), and
+    // 1 KB of alignment slack
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 18 * 1024;
     static_assert(STAGES >= 2, "at least two pipeline stages");
 };
 
@@ -390,6 +458,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     int* colEb = colE + 64;                    // 64 fixed-matrix column exponents
     float4* red = (float4*)(colEb + 64);       // [4 lane quarters][64 columns] reduction partials
     float2* lamf = (float2*)(red + 4 * 64);    // 64 lambda_q in FP32 (exponent estimates)
+    tfl* lamt = (tfl*)(lamf + 64);             // 64 x (Re, Im) lambda_q as exact triple-floats
+    RowInfo* rowinfo = (RowInfo*)(((uintptr_t)(lamt + 128) + 15) & ~(uintptr_t)15);   // [128]
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int bnc = args.bnc;
@@ -515,22 +585,6 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             const int64_t row0 = tile / ncol * NP;
             if (tile_skipped(args, row0, ct)) continue;
             unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
-            if (et < 64) {
-                colE[et] = 0;
-                colEb[et] = args.eb[ct * bnc + et];
-                if (MODE == EPI_DIVIDE) {
-                    const int q = ct * bnc + et;
-                    lamf[et] = q < n ? make_float2((float)args.lam[q].x, (float)args.lam[q].y)
-                                     : make_float2(0.f, 0.f);
-                }
-            }
-            if (et == 0) *stop = *(volatile int*)args.err;
-            epi_sync();
-            if (*stop) break;                                // uniform over the epilogue warps
-            if (trc && et == 0) trc[0] = global_ns();
-            const bool ok = tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout);
-            tc::fence_after_sync();
-            if (trc && et == 0) trc[1] = global_ns();         // accumulators complete
             const int qbase = ct * bnc;
             const int64_t o = row0 + rl;                      // local row of the launch
             const int ea = args.ea[o >> args.ea_shift];
@@ -555,21 +609,31 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 if (args.rp >= 1) firstp = dg[0];
             }
 
-            // EPI_DIVIDE / EPI_SLAB: sigma of the row p's minus lambda_i, multiplicity base and
-            // the length of the first run of equal p's
-            double2 sigma = make_double2(0, 0);
-            double mult_base = 1.0;
-            int run1 = 1;
-            if (MODE == EPI_DIVIDE || MODE == EPI_SLAB) {
+            // per-tile tables: column exponents, the fixed matrix's column exponents, lambda_q
+            // (FP32 and as exact triple-floats); per row (one thread of each row): sigma of the
+            // row p's minus lambda_i, the multiplicity base and the first run length
+            if (et < 64) {
+                colE[et] = 0;
+                colEb[et] = args.eb[qbase + et];
+                if (MODE == EPI_DIVIDE) {
+                    const int q = qbase + et;
+                    const double2 lq = q < n ? args.lam[q] : make_double2(0.0, 0.0);
+                    lamf[et] = make_float2((float)lq.x, (float)lq.y);
+                    lamt[2 * et] = to_tfl(lq.x);
+                    lamt[2 * et + 1] = to_tfl(lq.y);
+                }
+            }
+            if ((MODE == EPI_DIVIDE || MODE == EPI_SLAB) && grp == 0) {
+                double2 sg = make_double2(0, 0);
                 const int np_row = args.rp;
                 if (row_ok) {
 #pragma unroll
                     for (int m = 0; m < 7; ++m)
-                        if (m < np_row) sigma = cadd(sigma, args.lam[dg[m]]);
-                    sigma = csub(sigma, args.lam[args.i0 + (int)outer]);
+                        if (m < np_row) sg = cadd(sg, args.lam[dg[m]]);
+                    sg = csub(sg, args.lam[args.i0 + (int)outer]);
                 }
                 double denom = 1.0;
-                int run = 1;
+                int run = 1, r1 = 1;
                 bool first_run = true;
 #pragma unroll
                 for (int m = 1; m < 8; ++m) {
@@ -577,7 +641,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     if (m < np_row && dg[m] == dg[m - 1]) {
                         ++run;
                     } else {
-                        if (first_run) run1 = run;
+                        if (first_run) r1 = run;
                         first_run = false;
                         for (int u = 2; u <= run; ++u) denom *= u;
                         run = 1;
@@ -585,11 +649,36 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 }
                 double nf = 1.0;
                 for (int u = 2; u <= N; ++u) nf *= u;
-                mult_base = nf / denom;
+                RowInfo ri;
+                ri.sigma = sg;
+                ri.mult_base = nf / denom;
+                ri.run1 = r1;
+                ri.sr = to_tfl(sg.x);
+                ri.si = to_tfl(sg.y);
+                const double f = args.invfact * ri.mult_base;
+                ri.f_row = to_dfl(f);
+                ri.f_first = to_dfl(f / (r1 + 1));
+                rowinfo[rl] = ri;
             }
+            if (et == 0) *stop = *(volatile int*)args.err;
+            epi_sync();
+            if (*stop) break;                                // uniform over the epilogue warps
+            double2 sigma = make_double2(0, 0);
+            double mult_base = 1.0;
+            int run1 = 1;
+            if (MODE == EPI_DIVIDE || MODE == EPI_SLAB) {
+                sigma = rowinfo[rl].sigma;
+                mult_base = rowinfo[rl].mult_base;
+                run1 = rowinfo[rl].run1;
+            }
+            if (trc && et == 0) trc[0] = global_ns();
+            const bool ok = tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout);
+            tc::fence_after_sync();
+            if (trc && et == 0) trc[1] = global_ns();         // accumulators complete
 
-            // h of one element (EPI_DIVIDE / EPI_SLAB): V * 2^(ea+eb-VEXP) / N! (times the
-            // multiplicity for the reduction), divided by the clamped denominator in FP64
+            // h of one element in native FP64 (EPI_SLAB, and EPI_DIVIDE with fp64_quotient):
+            // V * 2^(ea+eb-VEXP) / N! (times the multiplicity for the reduction), divided by the
+            // clamped denominator
             auto quotient = [&](long long Vr, long long Vi, int eb, int qc) -> double2 {
                 const double mult = (qc == firstp) ? mult_base / (run1 + 1) : mult_base;
                 const double sc = pow2d(ea + eb - VEXP) * args.invfact *
@@ -626,14 +715,18 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             const int cl = c4 + c;
                             const int qc = qbase + cl;
                             const int eb = colEb[cl];
-                            const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
-                            const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
+                            // upper bounds of |V_re|, |V_im| in units of 2^30 (V = (L0 + L1 + L2 +
+                            // L3) 2^30): the FP32 sum plus its worst rounding error
+                            const float br = level_bound(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
+                            const float bi = level_bound(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
                             const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
                             unsigned key = 0;
                             if (MODE == EPI_SLICE) {
-                                const int bl = max(bitlen64(Vr), bitlen64(Vi));
-                                if (valid && bl) key = (unsigned)(bl + ea + eb - VEXP + 8192);
-                            } else if (valid && (Vr | Vi)) {
+                                // bitlen(V) <= exponent(bound) + 30
+                                const float bm = fmaxf(br, bi);
+                                if (valid && bm > 0.f)
+                                    key = (unsigned)(f32_exponent(bm) + 30 + ea + eb - VEXP + 8192);
+                            } else if (valid && (br > 0.f || bi > 0.f)) {
                                 float lb = 1.0f;
                                 if (args.divide) {
                                     const float2 lq = lamf[cl];
@@ -642,17 +735,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                                                                 fabsf(lq.x) + fabsf(lq.y));
                                     lb = fmaxf(sqrtf(fmaf(dx, dx, dy * dy)) - del, (float)args.eps);
                                 }
-                                // |V| from 22-bit pieces (32-bit conversions only)
-                                const float fr = fmaf((float)(int)(Vr >> 22), 4194304.0f,
-                                                      (float)(int)(Vr & 0x3FFFFF));
-                                const float fi = fmaf((float)(int)(Vi >> 22), 4194304.0f,
-                                                      (float)(int)(Vi & 0x3FFFFF));
                                 const float fm = qc == firstp ? fmb / (float)(run1 + 1) : fmb;
-                                const float hm = sqrtf(fmaf(fr, fr, fi * fi)) * fm / lb *
+                                const float hm = sqrtf(fmaf(br, br, bi * bi)) * fm / lb *
                                                  (1.0f + 0.0009765625f);
-                                int e;
-                                frexpf(hm, &e);
-                                key = (unsigned)(e + ea + eb - VEXP + 8192);
+                                key = (unsigned)(f32_exponent(hm) + 30 + ea + eb - VEXP + 8192);
                             }
                             const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
                             if (lane == 0 && wmax) atomicMax(&colE[cl], (int)wmax);
@@ -746,10 +832,37 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         } else if (MODE == EPI_SLICE) {
                             const int sh = ea + eb - VEXP - E + 7 + 8 * (S - 1);
                             digit_pairs<S>(shift_round(Vr, sh), shift_round(Vi, sh), w);
-                        } else {
+                        } else if (args.fp64_quotient) {
                             const double2 h = quotient(Vr, Vi, eb, qc);
                             const double sc = pow2d(7 + 8 * (S - 1) - E);
                             digit_pairs<S>(__double2ll_rn(h.x * sc), __double2ll_rn(h.y * sc), w);
+                        } else {
+                            // W = V 2^-30 f / D 2^k in double-float arithmetic; D from exact
+                            // triple-float terms, so near-resonant cancellation stays exact
+                            const dfl vr = level_sum_df(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
+                            const dfl vi = level_sum_df(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
+                            dfl Dr = {1.f, 0.f}, Di = {0.f, 0.f};
+                            if (args.divide) {
+                                Dr = tfl_sum(rowinfo[rl].sr, lamt[2 * cl]);
+                                Di = tfl_sum(rowinfo[rl].si, lamt[2 * cl + 1]);
+                            }
+                            dfl m2 = df_add(df_mul(Dr, Dr), df_mul(Di, Di));
+                            if (args.divide && m2.hi < args.eps2f) {   // Alg. 2 step 9
+                                Dr = to_dfl(args.eps);
+                                Di = {0.f, 0.f};
+                                m2 = df_mul(Dr, Dr);
+                            }
+                            const float r0 = __frcp_rn(m2.hi);
+                            const dfl e1 = df_add(dfl{1.f, 0.f}, df_neg(df_mul(m2, dfl{r0, 0.f})));
+                            const dfl rcp = df_add(dfl{r0, 0.f}, df_mul(dfl{r0, 0.f}, e1));
+                            const dfl rf = df_mul(rcp, qc == firstp ? rowinfo[rl].f_first
+                                                                    : rowinfo[rl].f_row);
+                            const dfl nr = df_add(df_mul(vr, Dr), df_mul(vi, Di));
+                            const dfl ni = df_add(df_mul(vi, Dr), df_neg(df_mul(vr, Di)));
+                            const int k = ea + eb - VEXP + 30 + 7 + 8 * (S - 1) - E;
+                            const dfl qr = df_mul(nr, rf), qi = df_mul(ni, rf);
+                            digit_pairs<S>(df_round_i64(dfl{ldexpf(qr.hi, k), ldexpf(qr.lo, k)}),
+                                           df_round_i64(dfl{ldexpf(qi.hi, k), ldexpf(qi.lo, k)}), w);
                         }
                         uint32_t* dst = reinterpret_cast<uint32_t*>(args.out_planes) + rowp * (KP / 2) + rl;
 #pragma unroll
@@ -1273,6 +1386,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     base0.invfact = 1.0 / factorial(N);
     base0.eps = p.eps;
     base0.divide = p.divide;
+    base0.fp64_quotient = p.fp64_quotient;
+    base0.eps2f = (float)(p.eps * p.eps);
     base0.err = err;
     base0.bnc = p.tile_n;
     base0.ncol_tiles = NP / p.tile_n;

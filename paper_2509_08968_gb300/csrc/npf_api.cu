@@ -617,6 +617,9 @@ int npf_set_option(npf_handle* h, int key, double value)
             p.tile_n = v;
             break;
         }
+        case NPF_OPT_FP64_QUOTIENT:
+            p.fp64_quotient = value != 0.0;
+            break;
         default:
             npf::fail(NPF_ERR_ARG, "unknown option key");
         }

@@ -74,6 +74,7 @@ struct Plan {
     int slices = 0;                // 0 = default for the precision
     double eps = 1e-8;
     int divide = 1;
+    int fp64_quotient = 0;         // tensor-core divide epilogue: 1 = native FP64 quotient
     int tile_n = 64;               // complex columns per tensor-core tile; 0 = autotuned
     size_t mem_budget = 0;         // 0 = 80% of free memory at compute time
     cudaStream_t stream = nullptr;

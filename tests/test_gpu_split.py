@@ -145,3 +145,36 @@ def test_n120_order4_slabs_against_stored_oracle(npf):
     with make_plan(npf, sysm, 4, "split_bf16") as p:
         for pre, ref in zip(g["prefixes"], g["slabs"]):
             assert rel_fro(p.modal_slab(4, [int(x) for x in pre]), ref) < 1e-10
+
+
+@pytest.mark.parametrize("fp64q", [0, 1])
+@pytest.mark.parametrize("detune", [0.0, 5e-9, 2e-7])
+def test_resonance_clamp(npf, fp64q, detune):
+    """Identity eigenvectors and lambda_2 = 2 lambda_0 + detune: the denominator of (i = 2,
+    p = (0, 0)) is -detune; below eps = 1e-8 it is replaced by eps (Alg. 2 step 9), above it
+    divides as is. Both quotient forms of the tensor-core divide against the oracle."""
+    n, N = 6, 2
+    lam = np.array([-1 + 2j, -1 - 2j, -2 + 4j + detune, -2 - 4j + detune, -0.5 + 1j, -0.5 - 1j])
+    U = np.eye(n, dtype=np.complex128)
+    V = np.eye(n, dtype=np.complex128)
+    A2 = S.random_packed_tensor_dense_fill(n, N, 41)
+    ref = oracle.psiN(A2, n, N, U, V, lam, p1_block=n)
+    with npf.Plan(lam, U, V, N, precision="split_bf16") as p:
+        p.set_option(npf.OPT_FP64_QUOTIENT, fp64q)
+        p.set_tensor(N, A2)
+        got = p.term(N)
+    assert rel_fro(got, ref) < 1e-10, rel_fro(got, ref)
+    # the resonant entry dominates: |Psi_2[2, 0]| ~ |A| / (2 max(|D|, eps))
+    assert abs(ref[2, 0]) > 1e5
+
+
+def test_fp64_quotient_option_agrees(npf):
+    sysm = S.config_n60(3, orders=(3,))
+    ref = oracle.psiN(sysm.tensors[3], 60, 3, sysm.U, sysm.V, sysm.lam, p1_block=4)
+    out = {}
+    for q in (0, 1):
+        with make_plan(npf, sysm, 3, "split_bf16") as p:
+            p.set_option(npf.OPT_FP64_QUOTIENT, q)
+            out[q] = p.term(3)
+        assert rel_fro(out[q], ref) < TOL["split_bf16"], (q, rel_fro(out[q], ref))
+    assert rel_fro(out[0], out[1]) < 1e-11
