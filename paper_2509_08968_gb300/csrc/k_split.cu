@@ -672,7 +672,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 run1 = rowinfo[rl].run1;
             }
             if (trc && et == 0) trc[0] = global_ns();
-            const bool ok = tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout);
+            // warp-uniform (the epilogue's shuffles and TMEM loads are warp-collective)
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout));
             tc::fence_after_sync();
             if (trc && et == 0) trc[1] = global_ns();         // accumulators complete
 
@@ -749,7 +750,79 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 if (trc && et == 0) trc[2] = global_ns();
             }
 
-            if (ok) {
+            if (MODE == EPI_REDUCE && ok) {
+                // G[c'][k] psi_{p_{N-1} k} in double-float, summed over the warp's 32 rows by a
+                // transposing butterfly: the first two exchanges halve the columns each lane
+                // carries (4 -> 2 -> 1), the last three finish one column per lane group
+                int pin = 0;   // innermost row digit p_{N-1} (static indices)
+#pragma unroll
+                for (int m = 0; m < 7; ++m)
+                    if (m == N - 2) pin = dg[m];
+                const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+                for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
+                    uint32_t rv[4][4], iv[4][4];
+                    load_levels<S>(trow + c4, 128, rv);
+                    load_levels<S>(trow + bnc + c4, 128, iv);
+                    tc::tmem_wait_ld();
+                    dfl pr[4], pi[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int cl = c4 + c;
+                        const int qc = qbase + cl;
+                        pr[c] = {0.f, 0.f};
+                        pi[c] = {0.f, 0.f};
+                        const dfl vr = level_sum_df(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
+                        const dfl vi = level_sum_df(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
+                        if (row_ok && qc < n && (vr.hi != 0.f || vi.hi != 0.f)) {
+                            const int sc = ea + colEb[cl] - VEXP + 30;
+                            const dfl gr = {ldexpf(vr.hi, sc), ldexpf(vr.lo, sc)};
+                            const dfl gi = {ldexpf(vi.hi, sc), ldexpf(vi.lo, sc)};
+                            const float4 w = args.psi_df[(int64_t)pin * n + qc];
+                            const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
+                            pr[c] = df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi)));
+                            pi[c] = df_add(df_mul(gr, wi), df_mul(gi, wr));
+                        }
+                    }
+                    // exchange 1 (lanes 16 apart): keep columns {0,1} or {2,3}, send the others
+                    dfl kr[2], ki[2];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const dfl sr = b4 ? pr[j] : pr[j + 2], si = b4 ? pi[j] : pi[j + 2];
+                        const dfl mr = b4 ? pr[j + 2] : pr[j], mi = b4 ? pi[j + 2] : pi[j];
+                        const dfl rr2 = {__shfl_xor_sync(0xffffffffu, sr.hi, 16),
+                                         __shfl_xor_sync(0xffffffffu, sr.lo, 16)};
+                        const dfl ri2 = {__shfl_xor_sync(0xffffffffu, si.hi, 16),
+                                         __shfl_xor_sync(0xffffffffu, si.lo, 16)};
+                        kr[j] = df_add(mr, rr2);
+                        ki[j] = df_add(mi, ri2);
+                    }
+                    // exchange 2 (lanes 8 apart): keep one of the two
+                    dfl ar, ai;
+                    {
+                        const dfl sr = b3 ? kr[0] : kr[1], si = b3 ? ki[0] : ki[1];
+                        const dfl mr = b3 ? kr[1] : kr[0], mi = b3 ? ki[1] : ki[0];
+                        const dfl rr2 = {__shfl_xor_sync(0xffffffffu, sr.hi, 8),
+                                         __shfl_xor_sync(0xffffffffu, sr.lo, 8)};
+                        const dfl ri2 = {__shfl_xor_sync(0xffffffffu, si.hi, 8),
+                                         __shfl_xor_sync(0xffffffffu, si.lo, 8)};
+                        ar = df_add(mr, rr2);
+                        ai = df_add(mi, ri2);
+                    }
+#pragma unroll
+                    for (int off = 4; off > 0; off >>= 1) {
+                        const dfl orr = {__shfl_xor_sync(0xffffffffu, ar.hi, off),
+                                         __shfl_xor_sync(0xffffffffu, ar.lo, off)};
+                        const dfl oi = {__shfl_xor_sync(0xffffffffu, ai.hi, off),
+                                        __shfl_xor_sync(0xffffffffu, ai.lo, off)};
+                        ar = df_add(ar, orr);
+                        ai = df_add(ai, oi);
+                    }
+                    if ((lane & 7) == 0)   // lanes 0, 8, 16, 24 hold columns 0, 1, 2, 3
+                        red[q4 * 64 + c4 + (b4 ? 2 : 0) + (b3 ? 1 : 0)] =
+                            make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+                }
+            }
+            if (MODE != EPI_REDUCE && ok) {
                 // pass 2 (or the only pass): outputs
                 for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
                     uint32_t rv[4][4], iv[4][4];
@@ -763,34 +836,6 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         const int eb = colEb[cl];
                         const long long Vr = combine(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                         const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                        if (MODE == EPI_REDUCE) {
-                            // G[c'][k] psi_{p_{N-1} k} (double-float), summed over the warp's
-                            // 32 rows by shuffles; lane 0 keeps the warp's partial
-                            dfl pr = {0.f, 0.f}, pi = {0.f, 0.f};
-                            if (row_ok && qc < n && (Vr | Vi)) {
-                                const int sc = ea + eb - VEXP;
-                                const dfl gr = df_from_i64(Vr, sc), gi = df_from_i64(Vi, sc);
-                                int pin = 0;   // innermost digit p_{N-1} (static indices)
-#pragma unroll
-                                for (int m = 0; m < 7; ++m)
-                                    if (m == N - 2) pin = dg[m];
-                                const float4 w = args.psi_df[(int64_t)pin * n + qc];
-                                const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
-                                pr = df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi)));
-                                pi = df_add(df_mul(gr, wi), df_mul(gi, wr));
-                            }
-#pragma unroll
-                            for (int off = 16; off > 0; off >>= 1) {
-                                const dfl orr = {__shfl_xor_sync(0xffffffffu, pr.hi, off),
-                                                 __shfl_xor_sync(0xffffffffu, pr.lo, off)};
-                                const dfl oi = {__shfl_xor_sync(0xffffffffu, pi.hi, off),
-                                                __shfl_xor_sync(0xffffffffu, pi.lo, off)};
-                                pr = df_add(pr, orr);
-                                pi = df_add(pi, oi);
-                            }
-                            if (lane == 0) red[q4 * 64 + cl] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
-                            continue;
-                        }
                         if (qc >= args.npc) continue;
                         if (MODE == EPI_F64T) {
                             if (qc < n) {
