@@ -352,6 +352,7 @@ enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3, EPI_REDUCE = 4
 struct RowArgs {
     int a_rows;          // rows per plane in the A tensor map
     int kch;             // K' chunks of 32
+    int klast;           // 16-wide K' steps in the last chunk (1 or 2): the rest is padding
     const int* ea;       // row exponents, indexed by (local row) >> ea_shift
     int ea_shift;
     const int* eb;       // column exponents of the fixed matrix (256 entries)
@@ -427,6 +428,32 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
 {
     for (long long it = 0; it < tc::kWaitLimit; ++it)
         if (tc::mbar_try_wait(bar, parity)) return;
+}
+
+// One K' chunk of MMAs: every slice pair (s, u) with s + u < S into its level accumulator, NKS
+// 16-wide K steps (1 when the second half of the chunk is padding). FIRST: the chunk opens the
+// tile, so each level's first MMA overwrites instead of accumulating. The loops unroll into
+// straight-line MMAs with constant descriptor offsets (start address / 16 in the low half).
+template <int S, bool FIRST, int NKS>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t a_lo, uint32_t b_lo,
+                                            uint32_t idesc)
+{
+    using C = RowCfg<S>;
+    bool first[4] = {FIRST, FIRST, FIRST, FIRST};
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int u = 0; u < S - s; ++u) {
+            const int L = s + u < 3 ? s + u : 3;
+#pragma unroll
+            for (int ks = 0; ks < NKS; ++ks) {
+                const uint32_t ao = a_lo + (uint32_t)((s * C::A_TILE + ks * 32) >> 4);
+                const uint32_t bo = b_lo + (uint32_t)((u * C::B_TILE + ks * 32) >> 4);
+                if (first[L]) tc::mma_bf16_lohi<false>(tmem + L * 128, ao, bo, tc::kSdescSw64Hi, idesc);
+                else tc::mma_bf16_lohi<true>(tmem + L * 128, ao, bo, tc::kSdescSw64Hi, idesc);
+                first[L] = false;
+            }
+        }
 }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory"); }
@@ -538,7 +565,6 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 if (tile_skipped(args, row0, ct)) continue;
                 if (!tc::mbar_wait(tempty, (t & 1) ^ 1, args.err, kErrTimeout)) break;
                 tc::fence_after_sync();
-                bool first[4] = {true, true, true, true};
                 for (int kc = 0; kc < args.kch; ++kc, ++it) {
                     const int st = (int)(it % C::STAGES);
                     const uint32_t ph = (it / C::STAGES) & 1;
@@ -548,20 +574,16 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     }
                     tc::fence_after_sync();
                     const uint32_t aBase = tc::smem_u32(stage_base + st * C::STAGE_BYTES);
-                    const uint32_t bBase = aBase + S * C::A_TILE;
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-#pragma unroll
-                        for (int u = 0; u < S - s; ++u) {
-                            const int L = s + u < 3 ? s + u : 3;
-#pragma unroll
-                            for (int ks = 0; ks < BK / 16; ++ks) {
-                                const uint64_t ad = tc::sdesc_sw64(aBase + s * C::A_TILE + ks * 32);
-                                const uint64_t bd = tc::sdesc_sw64(bBase + u * C::B_TILE + ks * 32);
-                                tc::mma_bf16(tmem + L * 128, ad, bd, idesc, first[L] ? 0u : 1u);
-                                first[L] = false;
-                            }
-                        }
+                    const uint32_t a_lo = tc::sdesc_sw64_lo(aBase);
+                    const uint32_t b_lo = tc::sdesc_sw64_lo(aBase + S * C::A_TILE);
+                    const bool half = kc == args.kch - 1 && args.klast == 1;
+                    if (kc == 0) {
+                        if (half) issue_chunk<S, true, 1>(tmem, a_lo, b_lo, idesc);
+                        else issue_chunk<S, true, 2>(tmem, a_lo, b_lo, idesc);
+                    } else {
+                        if (half) issue_chunk<S, false, 1>(tmem, a_lo, b_lo, idesc);
+                        else issue_chunk<S, false, 2>(tmem, a_lo, b_lo, idesc);
+                    }
                     tc::mma_commit(&empty[st]);
                 }
                 if (!alive) break;
@@ -1030,7 +1052,10 @@ __global__ void k_expand(const uint4* __restrict__ rec, int64_t P, int n, int N,
             pad |= a[m] >= n;
             if (m < N - 2) unread |= a[m] >= n;   // the contraction skips these rows' tiles
         }
-        if (unread) continue;
+        // rows past n in the innermost row digit only feed their own (discarded) outputs, so
+        // they are left unwritten; K' entries past n are written as zeros (they meet the fixed
+        // matrix's zero rows, where stale bit patterns could be NaN)
+        if (unread || a[N - 2] >= n) continue;
         uint4 r0 = make_uint4(0, 0, 0, 0), r1 = make_uint4(0, 0, 0, 0);
         if (!pad) {
             sort_small(a, N);
@@ -1444,6 +1469,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
         RowArgs a = base0;
         a.a_rows = (int)Prows;
         a.kch = (n + BK - 1) / BK;   // K = j < n: chunks past n hold zeros only
+        a.klast = (n + 15) / 16 - 2 * (a.kch - 1);
         a.ea = so.at_e[N];
         a.ea_shift = 0;
         a.eb = so.psir_e;
@@ -1476,6 +1502,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
             RowArgs a = base0;
             a.a_rows = (int)t_rows;
             a.kch = (2 * n + BK - 1) / BK;   // K' = 2 p + re/im < 2 n
+            a.klast = (2 * n + 15) / 16 - 2 * (a.kch - 1);
             a.ea = c == 1 ? sE + i0 : E[cb];
             a.ea_shift = c == 1 ? 7 * (N - 1) : 0;
             a.eb = so.phi_e;
@@ -1504,6 +1531,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
         RowArgs a = base0;
         a.a_rows = (int)t_rows;
         a.kch = (2 * n + BK - 1) / BK;   // K' = 2 p + re/im < 2 n
+        a.klast = (2 * n + 15) / 16 - 2 * (a.kch - 1);
         a.ea = E[cb];
         a.ea_shift = 0;
         a.eb = so.red_e;

@@ -141,6 +141,29 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// The same with the shared-memory descriptors given as 32-bit halves (low: start address and
+// leading offset, high: stride offset, version, layout) and a fixed accumulate flag, so that a
+// loop of MMAs over one stage costs a 32-bit add per operand and the instruction.
+template <bool ACC>
+__device__ __forceinline__ void mma_bf16_lohi(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
+                                              uint32_t hi, uint32_t idesc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %3};\n\t"
+        "mov.b64 db, {%2, %3};\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "n"(ACC ? 1 : 0)
+        : "memory");
+}
+// Low and high halves of sdesc_sw64(saddr).
+__device__ __forceinline__ uint32_t sdesc_sw64_lo(uint32_t saddr)
+{
+    return ((saddr & 0x3FFFF) >> 4) | (1u << 16);
+}
+constexpr uint32_t kSdescSw64Hi = (512u >> 4) | (1u << 14) | (4u << 29);
+
 // Arrive once on `bar` when every tcgen05.mma issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
