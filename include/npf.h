@@ -128,6 +128,15 @@ int npf_set_option(npf_handle* h, int key, double value);
 /* The order-only term Psi_N (out[i*n + k], host or device), recomputed by this call. */
 int npf_get_term(npf_handle* h, int order, npf_c128* out);
 
+/* Mode-interaction NPFs of the excitation x(0) = delta e_k of each state k (Section II.A,
+ * Eqs. 6-9). With zeta = delta Psi[:, k] and the corrected modal coordinates
+ * z(0) = zeta - sum_N hN(zeta, .., zeta) (Eq. 7, the zeta* of Eq. 9; every order 2..order with a
+ * tensor), out[0][k*n + i] = pN1 = phi_ki z^i(0) and, for M = 2..order,
+ * out[M-1][k*n + i] = pNM = phi_ki sum_p hM^i_p z^{p_1}(0) .. z^{p_M}(0) (Eq. 8; zero when order M
+ * has no tensor). Summed over i and M they reproduce x^k(0) = delta up to O(delta^3) (Eq. 6).
+ * out: [order][n][n], host or device. The plan's Psi_M terms and NPF buffer are overwritten. */
+int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out);
+
 /* One modal slab h^i_{prefix, q}: out[i*n + q] for the fixed prefix p_1..p_{N-1} (N-1 ints in
  * [0, n)), every mode i and last index q. Host or device `out`. For parity checks at full size. */
 int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* out);

@@ -167,3 +167,38 @@ def npf_orders(sysm, order, eps=DEFAULT_EPS, p1_block=1):
         if m in sysm.tensors:
             S += psiN(sysm.tensors[m], n, m, sysm.U, sysm.V, sysm.lam, eps, True, p1_block)
     return npf(sysm.U, sysm.V, S)
+
+
+def reduce_weights(packed, n, N, U, V, lam, W, eps=DEFAULT_EPS, divide=True, p1_block=None):
+    """T[i, k] = sum_p h^i_p prod_m W[p_m, k]: the contraction of steps 12-19 with weight columns
+    W[:, k] in place of Psi[:, k] (h from the factorised form, with Psi on the upper index)."""
+    W = _c128(W)
+    p1_block = n if p1_block is None else p1_block
+    acc = np.zeros((n, n), dtype=np.complex128)
+    for lo in range(0, n, p1_block):
+        hi = min(n, lo + p1_block)
+        hb = h_fact(packed, n, N, U, V, lam, eps, divide, lo, hi)
+        _load().npfo_psiN_accumulate(n, N, _p(hb), _p(W), lo, hi, _p(acc))
+    return -acc
+
+
+def interaction_npfs(sysm, order, delta, eps=DEFAULT_EPS, p1_block=None):
+    """Mode-interaction NPFs of the excitation x(0) = delta e_k (Eqs. 6-9), [order, n, n]:
+    [0][k, i] = pN1 = phi_ki z^i(0) with z(0) = zeta - sum_N hN(zeta..zeta), zeta = delta Psi[:, k]
+    (Eq. 7; Psi_N as computed by psiN already carries the minus sign); [M-1][k, i] = pNM =
+    phi_ki sum_p hM^i_p prod_m zeta*_{p_m} with zeta* = z(0) (Eqs. 8-9), zero without an order-M
+    tensor."""
+    n = sysm.n
+    U, V = _c128(sysm.U), _c128(sysm.V)
+    z = delta * V
+    for N in range(2, order + 1):
+        if N in sysm.tensors:
+            z = z + delta ** N * psiN(sysm.tensors[N], n, N, U, V, sysm.lam, eps, True,
+                                      p1_block or n)
+    out = np.zeros((order, n, n), dtype=np.complex128)
+    out[0] = U * z.T
+    for M in range(2, order + 1):
+        if M in sysm.tensors:
+            T = reduce_weights(sysm.tensors[M], n, M, U, V, sysm.lam, z, eps, True, p1_block)
+            out[M - 1] = U * T.T
+    return out

@@ -72,6 +72,7 @@ def load():
     lib.npf_set_option.argtypes = [vp, ci, cd]
     lib.npf_get_term.argtypes = [vp, ci, vp]
     lib.npf_get_modal_slab.argtypes = [vp, ci, vp, vp]
+    lib.npf_interaction.argtypes = [vp, ci, cd, vp]
     lib.npf_batch_compute.argtypes = [ci, vp, vp, vp]
     lib.npf_last_error.restype = ctypes.c_char_p
     lib.npf_last_status.restype = ci
@@ -169,6 +170,14 @@ class Plan:
         if out is None:
             out = np.empty((self.n, self.n), dtype=np.complex128)
         _check(load().npf_get_term(self._h, order, _ptr(out)))
+        return out
+
+    def interaction(self, order, delta, out=None):
+        """Mode-interaction NPFs [order, n, n]: [0] = pN1, [M-1] = pNM (Eqs. 6-9) for the
+        excitation delta e_k of each state k."""
+        if out is None:
+            out = np.empty((order, self.n, self.n), dtype=np.complex128)
+        _check(load().npf_interaction(self._h, order, float(delta), _ptr(out)))
         return out
 
     def modal_slab(self, order, prefix, out=None):

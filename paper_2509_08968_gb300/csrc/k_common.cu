@@ -164,6 +164,39 @@ void launch_add(Plan& p, double2* acc, const double2* x, int64_t count)
     NPF_CUDA(cudaGetLastError());
 }
 
+__global__ void k_axpy(double2* y, double a, const double2* x, double b, int64_t count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 u = x[i], v = y[i];
+        y[i] = make_double2(fma(a, u.x, b * v.x), fma(a, u.y, b * v.y));
+    }
+}
+void launch_axpy(Plan& p, double2* y, double a, const double2* x, double b, int64_t count)
+{
+    LaunchScope ls(&p.prof, "axpy", p.stream);
+    const int blocks = (int)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096);
+    k_axpy<<<blocks > 0 ? blocks : 1, 256, 0, p.stream>>>(y, a, x, b, count);
+    NPF_CUDA(cudaGetLastError());
+}
+
+// out[k][i] = sign * phi_{k i} * Z[i][k] (the elementwise product of step 20 with a modal matrix)
+__global__ void k_hadamard_t(int n, double sign, const double2* U, const double2* Z, double2* out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    const int k = (int)(t / n), i = (int)(t % n);
+    const double2 v = cmul(U[t], Z[(int64_t)i * n + k]);
+    out[t] = make_double2(sign * v.x, sign * v.y);
+}
+void launch_hadamard_t(Plan& p, double sign, const double2* Z, double2* out)
+{
+    LaunchScope ls(&p.prof, "hadamard", p.stream);
+    const int64_t nn = (int64_t)p.n * p.n;
+    k_hadamard_t<<<(unsigned)((nn + 255) / 256), 256, 0, p.stream>>>(p.n, sign, p.d_U, Z, out);
+    NPF_CUDA(cudaGetLastError());
+}
+
 // cnt[r*(n+1) + v] = C(n - v + r - 1, r): non-decreasing r-tuples with values in [v, n).
 void build_cnt_table(Plan& p)
 {

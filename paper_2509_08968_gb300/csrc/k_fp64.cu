@@ -192,8 +192,9 @@ static DivideArgs divide_args(const Plan& p, int N)
 }
 
 // Psi_N for one order, native FP64.
-void fp64_term(Plan& p, int N, double2* d_out)
+void fp64_term(Plan& p, int N, double2* d_out, const double2* W)
 {
+    const double2* Wr = W ? W : p.d_V;   // reduction weights W[p][k]
     const int n = p.n;
     const int64_t nN = ipow64(n, N);
     const int64_t P = p.packed_count[N];
@@ -242,7 +243,7 @@ void fp64_term(Plan& p, int N, double2* d_out)
         for (int i0 = 0; i0 < n; i0 += nb) {
             const int c = std::min(nb, n - i0);
             gemm(p, "fp64_reduce_gemm", X + (int64_t)i0 * nN1 * cur, (int64_t)c * nN1, cur,
-                 p.d_V + (int64_t)b0 * n, n, n, Y, 1, none);
+                 Wr + (int64_t)b0 * n, n, n, Y, 1, none);
             double2* src = Y;
             double2* dst = bufC;
             int64_t O = (int64_t)c * nN1 / n;  // rows after removing p_{N-1}
@@ -251,7 +252,7 @@ void fp64_term(Plan& p, int N, double2* d_out)
                 const bool last = (m == 1);
                 const int64_t cnt = O * n;
                 k64_diag<<<(unsigned)((cnt + 255) / 256), 256, 0, p.stream>>>(
-                    n, O, n, 0, src, p.d_V, last ? d_out + (int64_t)i0 * n : dst, last ? 1 : 0);
+                    n, O, n, 0, src, Wr, last ? d_out + (int64_t)i0 * n : dst, last ? 1 : 0);
                 NPF_CUDA(cudaGetLastError());
                 if (!last) { std::swap(src, dst); O /= n; }
             }

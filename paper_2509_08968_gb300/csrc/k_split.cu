@@ -1085,6 +1085,10 @@ struct SplitOperand {
     int64_t at_rows[kMaxOrder + 1] = {};
     const double* at_src[kMaxOrder + 1] = {};
     int* err = nullptr;
+    // reduction weights other than Psi (mode-interaction NPFs): planes of W^T, exponents, W in
+    // double-float
+    __nv_bfloat16* wred = nullptr;  int* wred_e = nullptr;
+    float4* w_df = nullptr;
 };
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -1205,6 +1209,7 @@ void split_release(Plan& p)
     cudaFree(so->red); cudaFree(so->red_e);
     cudaFree(so->psi_df);
     for (int N = 0; N <= kMaxOrder; ++N) { cudaFree(so->at[N]); cudaFree(so->at_e[N]); }
+    cudaFree(so->wred); cudaFree(so->wred_e); cudaFree(so->w_df);
     cudaFree(so->err);
     delete so;
     p.split = nullptr;
@@ -1276,6 +1281,26 @@ static SplitOperand& prepare(Plan& p)
     NPF_CUDA(cudaMalloc(&so->err, sizeof(int)));
     NPF_CUDA(cudaMemset(so->err, 0, sizeof(int)));
     return *so;
+}
+
+// Slices of a reduction-weight matrix W[p][k] (device, n x n) in place of Psi: the fixed matrix
+// of the reduction GEMM (rows k, complex K index p), its exponents, and W in double-float.
+static void prepare_weights(Plan& p, SplitOperand& so, const double2* dW)
+{
+    const int n = p.n, S = so.S;
+    std::vector<double2> W((size_t)n * n);
+    NPF_CUDA(cudaMemcpy(W.data(), dW, W.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    std::vector<uint16_t> planes;
+    std::vector<int> ex;
+    build_fixed(n, S, true, [&](int pidx, int k) { return W[(size_t)pidx * n + k]; }, planes, ex);
+    put(so.wred, planes);
+    put(so.wred_e, ex);
+    std::vector<float4> wdf((size_t)n * n);
+    for (size_t t = 0; t < wdf.size(); ++t) {
+        const float rh = (float)W[t].x, ih = (float)W[t].y;
+        wdf[t] = make_float4(rh, (float)(W[t].x - rh), ih, (float)(W[t].y - ih));
+    }
+    put(so.w_df, wdf);
 }
 
 void split_refresh_modes(Plan& p)
@@ -1403,9 +1428,10 @@ static double factorial(int N) { double f = 1; for (int t = 2; t <= N; ++t) f *=
 // Device memory of one order: S (FP64, n x P), records (n x P x 32 B), and per i of a batch two
 // operand buffers of NP^(N-1) rows x 256 K' x S planes (BF16) plus exponents.
 template <int S>
-static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
+static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const double2* W)
 {
     SplitOperand& so = prepare(p);
+    if (W) prepare_weights(p, so, W);
     set_smem_attrs<S>();
     prepare_tensor<S>(p, so, N);
     int* const err = p.err_override ? p.err_override : so.err;   // a batch zeroes and checks its own
@@ -1441,7 +1467,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
 
     const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, p.tile_n);
     const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, p.tile_n);
-    const CUtensorMap tRed = make_tmap(so.red, KP, (int64_t)S * 512, p.tile_n);
+    const CUtensorMap tRed = make_tmap(W ? so.wred : so.red, KP, (int64_t)S * 512, p.tile_n);
     const CUtensorMap tAT = make_tmap(so.at[N], NP, (int64_t)S * Prows, 128);
     const CUtensorMap tT0 = make_tmap(T[0], KP, (int64_t)S * t_rows, 128);
     const CUtensorMap tT1 = make_tmap(T[1], KP, (int64_t)S * t_rows, 128);
@@ -1450,8 +1476,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     RowArgs base0{};
     base0.n = n;
     base0.N = N;
-    base0.V = p.d_V;
-    base0.psi_df = so.psi_df;
+    base0.V = W ? W : p.d_V;              // reduction weights (the prefix factors)
+    base0.psi_df = W ? so.w_df : so.psi_df;
     base0.lam = p.d_lam;
     base0.invfact = 1.0 / factorial(N);
     base0.eps = p.eps;
@@ -1534,7 +1560,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
         a.klast = (2 * n + 15) / 16 - 2 * (a.kch - 1);
         a.ea = E[cb];
         a.ea_shift = 0;
-        a.eb = so.red_e;
+        a.eb = W ? so.wred_e : so.red_e;
         a.num_tiles = rows / NP * a.ncol_tiles;
         a.digits = 1;
         a.rp = N - 1;
@@ -1552,21 +1578,21 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix)
     if (herr) fail(NPF_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
 }
 
-static void split_any(Plan& p, int N, double2* d_out, const int* prefix)
+static void split_any(Plan& p, int N, double2* d_out, const int* prefix, const double2* W)
 {
     if (N < 2) fail(NPF_ERR_ARG, "order must be >= 2");
     if (N > 4) fail(NPF_ERR_UNSUPPORTED, "the tensor-core path supports orders <= 4 (use NPF_PREC_FP64)");
     switch (default_slices(p)) {
-    case 2: split_run<2>(p, N, d_out, prefix); break;
-    case 3: split_run<3>(p, N, d_out, prefix); break;
-    case 4: split_run<4>(p, N, d_out, prefix); break;
-    case 5: split_run<5>(p, N, d_out, prefix); break;
-    case 6: split_run<6>(p, N, d_out, prefix); break;
+    case 2: split_run<2>(p, N, d_out, prefix, W); break;
+    case 3: split_run<3>(p, N, d_out, prefix, W); break;
+    case 4: split_run<4>(p, N, d_out, prefix, W); break;
+    case 5: split_run<5>(p, N, d_out, prefix, W); break;
+    case 6: split_run<6>(p, N, d_out, prefix, W); break;
     default: fail(NPF_ERR_UNSUPPORTED, "slices must be in [2, 6] on the tensor-core path");
     }
 }
 
-void split_term(Plan& p, int N, double2* d_out) { split_any(p, N, d_out, nullptr); }
-void split_slab(Plan& p, int N, const int* prefix, double2* d_out) { split_any(p, N, d_out, prefix); }
+void split_term(Plan& p, int N, double2* d_out, const double2* W) { split_any(p, N, d_out, nullptr, W); }
+void split_slab(Plan& p, int N, const int* prefix, double2* d_out) { split_any(p, N, d_out, prefix, nullptr); }
 
 }  // namespace npf

@@ -170,19 +170,20 @@ int tuned_tile(Plan& p, int N)
     return best_tile;
 }
 
-void compute_term(Plan& p, int N, double2* out)
+// -sum_p h^i_p prod_m W[p_m][k] into out (W = nullptr: the left eigenvectors, i.e. Psi_N).
+void compute_term(Plan& p, int N, double2* out, const double2* W = nullptr)
 {
     if (p.precision == NPF_PREC_FP64) {
-        npf::fp64_term(p, N, out);
+        npf::fp64_term(p, N, out, W);
         return;
     }
     if (p.tile_n != 0) {
-        npf::split_term(p, N, out);
+        npf::split_term(p, N, out, W);
         return;
     }
     p.tile_n = tuned_tile(p, N);
     try {
-        npf::split_term(p, N, out);
+        npf::split_term(p, N, out, W);
     } catch (...) {
         p.tile_n = 0;
         throw;
@@ -522,6 +523,42 @@ int npf_compute(npf_handle* h, int order, npf_c128* out)
         NPF_CUDA(cudaMemcpyAsync(out, p.d_npf, (size_t)p.n * p.n * sizeof(double2),
                                  cudaMemcpyDefault, p.stream));
         sync(p);
+    });
+}
+
+int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out)
+{
+    return guarded([&] {
+        if (!h || !out) npf::fail(NPF_ERR_ARG, "null handle or out");
+        Plan& p = h->p;
+        if (order < 1 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [1, N_max]");
+        if (!(delta > 0.0)) npf::fail(NPF_ERR_ARG, "delta must be > 0");
+        const int64_t nn = (int64_t)p.n * p.n;
+        // z(0) = delta Psi + sum_M delta^M Psi_M (Eq. 7; Eq. 9's corrected coordinates), kept in
+        // d_sum; the per-order results go to d_npf as scratch before the copies
+        double2* z = p.d_sum;
+        for (int M = 2; M <= order; ++M)
+            if (p.d_tensor[M]) compute_term(p, M, p.d_psiN[M]);
+        npf::launch_axpy(p, z, delta, p.d_V, 0.0, nn);
+        for (int M = 2; M <= order; ++M)
+            if (p.d_tensor[M]) npf::launch_axpy(p, z, std::pow(delta, M), p.d_psiN[M], 1.0, nn);
+        // pN1[k][i] = phi_ki z^i(0)
+        npf::launch_hadamard_t(p, 1.0, z, p.d_npf);
+        NPF_CUDA(cudaMemcpyAsync(out, p.d_npf, nn * sizeof(double2), cudaMemcpyDefault, p.stream));
+        sync(p);
+        for (int M = 2; M <= order; ++M) {
+            npf_c128* dst = out + (int64_t)(M - 1) * nn;
+            if (!p.d_tensor[M]) {
+                NPF_CUDA(cudaMemsetAsync(p.d_npf, 0, nn * sizeof(double2), p.stream));
+            } else {
+                // pNM[k][i] = phi_ki sum_p hM^i_p prod_m z^{p_m}(0) (Eq. 8) = -phi_ki T[i][k]
+                // with T the order-M reduction against the weights W = z(0)
+                compute_term(p, M, p.d_psiN[M], z);
+                npf::launch_hadamard_t(p, -1.0, p.d_psiN[M], p.d_npf);
+            }
+            NPF_CUDA(cudaMemcpyAsync(dst, p.d_npf, nn * sizeof(double2), cudaMemcpyDefault, p.stream));
+            sync(p);
+        }
     });
 }
 

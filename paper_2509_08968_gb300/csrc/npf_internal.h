@@ -117,13 +117,14 @@ size_t effective_budget(const Plan& p);
 // ----------------------------------------------------------------------------------------
 // Native FP64 path (k_fp64.cu).
 // ----------------------------------------------------------------------------------------
-void fp64_term(Plan& p, int N, double2* d_out /* Psi_N [n][n] */);
+// Psi_N [n][n] = -sum_p h^i_p prod_m W[p_m][k]; W = nullptr: the left eigenvectors (W = V).
+void fp64_term(Plan& p, int N, double2* d_out, const double2* W = nullptr);
 void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out /* h [n][n] */);
 
 // ----------------------------------------------------------------------------------------
 // Split BF16 tensor-core path (k_split.cu).
 // ----------------------------------------------------------------------------------------
-void split_term(Plan& p, int N, double2* d_out);
+void split_term(Plan& p, int N, double2* d_out, const double2* W = nullptr);
 void split_slab(Plan& p, int N, const int* prefix, double2* d_out);
 void split_release(Plan& p);
 void split_prepare_tensor(Plan& p, int N);   // digit planes of a newly uploaded tensor
@@ -136,6 +137,8 @@ void split_refresh_modes(Plan& p);   // new modal data of the same size: re-slic
 void launch_finish(Plan& p, const double2* d_sum, double2* d_npf);   // NPF = phi o (psi + S)^T
 void launch_zero(Plan& p, double2* d, int64_t count);
 void launch_add(Plan& p, double2* acc, const double2* x, int64_t count);
+void launch_axpy(Plan& p, double2* y, double a, const double2* x, double b, int64_t count);   // y = a x + b y
+void launch_hadamard_t(Plan& p, double sign, const double2* Z, double2* out);   // out[k][i] = sign U[k][i] Z[i][k]
 void build_cnt_table(Plan& p);
 void note_launches(int64_t k);   // k more kernels launched (graph replays)
 
