@@ -110,6 +110,15 @@ npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* 
  * the paper: for sweeps over operating points of one model. */
 int npf_set_modes(npf_handle* h, const npf_c128* eigvals, const npf_c128* U, const npf_c128* V);
 
+/* Critical-mode subset (the reduction suggested in Section III): with m > 0 the modal indices
+ * i, p_1..p_N of Eq. 4 and the sums of Eq. 7 run over the m listed modes only (modes[m],
+ * distinct, in [0, n)); the states and the tensor are unchanged, so the work drops from
+ * ~n^(N+2) to ~n m^(N+1). NPF columns (modes) outside the subset then carry the linear PF only,
+ * and npf_get_term rows outside it are zero. m = 0 (or n) restores all modes. Tensor-core forms
+ * only: the native FP64 form and npf_get_modal_slab return NPF_ERR_UNSUPPORTED while a subset
+ * is set. Not in the paper beyond that remark. */
+int npf_set_mode_subset(npf_handle* h, int m, const int* modes);
+
 /* Copy the packed order-`order` tensor (2 <= order <= N_max; layout above; host or device) into
  * the plan's device memory. Replaces a previous tensor of that order. */
 int npf_set_tensor(npf_handle* h, int order, const double* coeffs);

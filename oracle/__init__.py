@@ -202,3 +202,16 @@ def interaction_npfs(sysm, order, delta, eps=DEFAULT_EPS, p1_block=None):
             T = reduce_weights(sysm.tensors[M], n, M, U, V, sysm.lam, z, eps, True, p1_block)
             out[M - 1] = U * T.T
     return out
+
+
+def psiN_subset(packed, n, N, U, V, lam, modes, eps=DEFAULT_EPS, p1_block=None):
+    """Psi_N restricted to a set of modes: for i in `modes`,
+    -sum_{p in modes^N} h^i_p prod_m psi_{p_m k} (the sums of Eq. 7 over the subset only); rows of
+    the other modes are zero. h^i_p itself does not depend on the subset (Eq. 4)."""
+    modes = np.asarray(modes)
+    W = np.zeros((n, n), dtype=np.complex128)
+    W[modes] = _c128(V)[modes]
+    T = reduce_weights(packed, n, N, U, V, lam, W, eps, True, p1_block)
+    out = np.zeros((n, n), dtype=np.complex128)
+    out[modes] = -T[modes]
+    return out

@@ -55,6 +55,7 @@ def load():
     lib.npf_plan.argtypes = [ci, ci, vp, vp, vp, sz]
     lib.npf_set_tensor.argtypes = [vp, ci, vp]
     lib.npf_set_modes.argtypes = [vp, vp, vp, vp]
+    lib.npf_set_mode_subset.argtypes = [vp, ci, vp]
     lib.npf_mlp_create.restype = vp
     lib.npf_mlp_create.argtypes = [ci, ci, vp, vp, vp]
     lib.npf_mlp_param_count.restype = i64
@@ -150,6 +151,14 @@ class Plan:
         if not _is_torch(lam):
             lam, U, V = _host_c128(lam), _host_c128(U), _host_c128(V)
         _check(load().npf_set_modes(self._h, _ptr(lam), _ptr(U), _ptr(V)))
+
+    def set_mode_subset(self, modes=None):
+        """Restrict the modal indices to `modes` (None or all modes: no restriction)."""
+        if modes is None:
+            _check(load().npf_set_mode_subset(self._h, 0, None))
+            return
+        m = np.ascontiguousarray(np.asarray(modes, dtype=np.int32))
+        _check(load().npf_set_mode_subset(self._h, int(m.size), _ptr(m)))
 
     def set_tensor(self, order, coeffs):
         """Packed symmetric order-`order` tensor [n, C(n+order-1, order)] float64."""

@@ -197,6 +197,23 @@ void launch_hadamard_t(Plan& p, double sign, const double2* Z, double2* out)
     NPF_CUDA(cudaGetLastError());
 }
 
+__global__ void k_unpermute(int n, const int* perm, const double2* in, double2* out, int columns)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    const int r = (int)(t / n), c = (int)(t % n);
+    if (columns) out[(int64_t)r * n + perm[c]] = in[t];
+    else out[(int64_t)perm[r] * n + c] = in[t];
+}
+void launch_unpermute(Plan& p, const double2* in, double2* out, bool columns)
+{
+    LaunchScope ls(&p.prof, "unpermute", p.stream);
+    const int64_t nn = (int64_t)p.n * p.n;
+    k_unpermute<<<(unsigned)((nn + 255) / 256), 256, 0, p.stream>>>(p.n, p.d_perm, in, out,
+                                                                     columns ? 1 : 0);
+    NPF_CUDA(cudaGetLastError());
+}
+
 // cnt[r*(n+1) + v] = C(n - v + r - 1, r): non-decreasing r-tuples with values in [v, n).
 void build_cnt_table(Plan& p)
 {

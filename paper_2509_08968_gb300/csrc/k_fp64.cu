@@ -194,6 +194,8 @@ static DivideArgs divide_args(const Plan& p, int N)
 // Psi_N for one order, native FP64.
 void fp64_term(Plan& p, int N, double2* d_out, const double2* W)
 {
+    if (p.nm != p.n)
+        fail(NPF_ERR_UNSUPPORTED, "a critical-mode subset needs the tensor-core forms");
     const double2* Wr = W ? W : p.d_V;   // reduction weights W[p][k]
     const int n = p.n;
     const int64_t nN = ipow64(n, N);

@@ -365,7 +365,9 @@ struct RowArgs {
     int colmask;         // new column must be <= the first p
     int64_t R;           // rows per outer index (output layout [outer][q][r])
     int npc;             // extent of the new index in the output layout
-    int n;
+    int n;               // states (range of the a digits and of the reduction's columns k)
+    int nm;              // modes in use (range of i and of the p digits; n unless a subset is set)
+    int ncv;             // valid columns of this launch (modes, or states for the reduction)
     __nv_bfloat16* out_planes;
     int64_t out_plane_stride;
     int* out_exp;
@@ -407,7 +409,7 @@ struct RowCfg {
 
 __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_local, int ct)
 {
-    if (ct * a.bnc >= a.n) return true;                    // every column is padding
+    if (ct * a.bnc >= a.ncv) return true;                  // every column is padding
     if (!a.digits) return false;
     int d[8];
     row_digits(row0_local % a.R, a.N - 1, d);
@@ -415,7 +417,7 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_loca
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
         if (m + 1 >= nd) break;                            // shared digits: 0 .. nd-2
-        if (d[m] >= a.n) return true;                      // padding index: rows are zero
+        if (d[m] >= (m < a.rp ? a.nm : a.n)) return true;  // padding index: rows are zero
         if (m >= 1 && m < a.rp && d[m - 1] > d[m]) return true;
     }
     const bool first_shared = a.rp >= 1 && nd >= 2;
@@ -624,7 +626,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 #pragma unroll
                 for (int m = 0; m < 7; ++m) {
                     if (m < N - 1) {
-                        row_ok &= dg[m] < n;
+                        row_ok &= dg[m] < (m < args.rp ? args.nm : n);
                         if (m >= 1 && m < args.rp) row_ok &= dg[m - 1] <= dg[m];
                     }
                 }
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 colEb[et] = args.eb[qbase + et];
                 if (MODE == EPI_DIVIDE) {
                     const int q = qbase + et;
-                    const double2 lq = q < n ? args.lam[q] : make_double2(0.0, 0.0);
+                    const double2 lq = q < args.ncv ? args.lam[q] : make_double2(0.0, 0.0);
                     lamf[et] = make_float2((float)lq.x, (float)lq.y);
                     lamt[2 * et] = to_tfl(lq.x);
                     lamt[2 * et + 1] = to_tfl(lq.y);
@@ -742,7 +744,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             // L3) 2^30): the FP32 sum plus its worst rounding error
                             const float br = level_bound(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                             const float bi = level_bound(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                            const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
+                            const bool valid = row_ok && qc < args.ncv && (!args.colmask || qc <= firstp);
                             unsigned key = 0;
                             if (MODE == EPI_SLICE) {
                                 // bitlen(V) <= exponent(bound) + 30
@@ -795,7 +797,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         pi[c] = {0.f, 0.f};
                         const dfl vr = level_sum_df(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                         const dfl vi = level_sum_df(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                        if (row_ok && qc < n && (vr.hi != 0.f || vi.hi != 0.f)) {
+                        if (row_ok && qc < args.ncv && (vr.hi != 0.f || vi.hi != 0.f)) {
                             const int sc = ea + colEb[cl] - VEXP + 30;
                             const dfl gr = {ldexpf(vr.hi, sc), ldexpf(vr.lo, sc)};
                             const dfl gi = {ldexpf(vi.hi, sc), ldexpf(vi.lo, sc)};
@@ -860,14 +862,14 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         const long long Vi = combine(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
                         if (qc >= args.npc) continue;
                         if (MODE == EPI_F64T) {
-                            if (qc < n) {
+                            if (qc < args.ncv) {
                                 const double sc = pow2d(ea + eb - VEXP);
                                 args.out_f64[(int64_t)qc * args.ld_f64 + o] =
                                     make_double2((double)Vr * sc, (double)Vi * sc);
                             }
                             continue;
                         }
-                        const bool valid = row_ok && qc < n && (!args.colmask || qc <= firstp);
+                        const bool valid = row_ok && qc < args.ncv && (!args.colmask || qc <= firstp);
                         if (MODE == EPI_SLAB) {
                             // store h^i_{pre, q} when the multiset (q, row p's) minus pre is {extra}
                             if (!valid || !(Vr | Vi)) continue;
@@ -944,7 +946,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 epi_sync();
                 const int cl = et;
                 const int qc = qbase + cl;
-                if (ok && cl < bnc && qc < n) {
+                if (ok && cl < bnc && qc < args.ncv) {
                     dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
                     for (int pp = 0; pp < 4; ++pp) {
                         const float4 g = red[pp * 64 + cl];
@@ -1437,6 +1439,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     int* const err = p.err_override ? p.err_override : so.err;   // a batch zeroes and checks its own
     if (!p.err_override) NPF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), p.stream));
     const int n = p.n;
+    const int nm = p.nm;                 // modes in use (a critical-mode subset comes first)
     const int64_t P = p.packed_count[N];
     const int64_t Prows = so.at_rows[N];
     const int64_t npN1 = ipow64(NP, N - 1);
@@ -1449,7 +1452,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const size_t budget = effective_budget(p);
     if (s_bytes + rec_bytes + per_i > budget)
         fail(NPF_ERR_OOM, "memory budget too small for one upper-index batch");
-    const int ib = (int)std::min<size_t>((size_t)n, (budget - s_bytes - rec_bytes) / per_i);
+    const int ib = (int)std::min<size_t>((size_t)nm, (budget - s_bytes - rec_bytes) / per_i);
     const int64_t t_rows = (int64_t)ib * npN1;
     const size_t tbytes = (size_t)t_rows * KP * 2 * S;
     const size_t ebytes = (size_t)t_rows * 4;
@@ -1475,6 +1478,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
 
     RowArgs base0{};
     base0.n = n;
+    base0.nm = nm;
+    base0.ncv = nm;
     base0.N = N;
     base0.V = W ? W : p.d_V;              // reduction weights (the prefix factors)
     base0.psi_df = W ? so.w_df : so.psi_df;
@@ -1509,13 +1514,13 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     }
     {
         LaunchScope ls(&p.prof, "split_s_records", p.stream);
-        k_s_exp<<<n, 256, 0, p.stream>>>(Sd, Prows, P, sE);
-        k_s_records<S><<<4096, 256, 0, p.stream>>>(Sd, Prows, P, n, sE, rec);
+        k_s_exp<<<nm, 256, 0, p.stream>>>(Sd, Prows, P, sE);
+        k_s_records<S><<<4096, 256, 0, p.stream>>>(Sd, Prows, P, nm, sE, rec);
         NPF_CUDA(cudaGetLastError());
     }
 
-    for (int i0 = 0; i0 < n; i0 += ib) {
-        const int cur = std::min(ib, n - i0);
+    for (int i0 = 0; i0 < nm; i0 += ib) {
+        const int cur = std::min(ib, nm - i0);
         const int64_t rows = (int64_t)cur * npN1;
         {
             LaunchScope ls(&p.prof, "split_expand", p.stream);
@@ -1556,8 +1561,9 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         // ---- reduction: rows c' = (i, p_1..p_{N-1}), K = p_N, columns k (Psi^T)
         RowArgs a = base0;
         a.a_rows = (int)t_rows;
-        a.kch = (2 * n + BK - 1) / BK;   // K' = 2 p + re/im < 2 n
-        a.klast = (2 * n + 15) / 16 - 2 * (a.kch - 1);
+        a.kch = (2 * nm + BK - 1) / BK;   // K' = 2 p_N + re/im < 2 nm
+        a.klast = (2 * nm + 15) / 16 - 2 * (a.kch - 1);
+        a.ncv = n;                         // columns: states k
         a.ea = E[cb];
         a.ea_shift = 0;
         a.eb = W ? so.wred_e : so.red_e;

@@ -73,11 +73,38 @@ void free_plan(Plan& p)
     }
     cudaFree(p.d_npf);
     cudaFree(p.d_sum);
+    cudaFree(p.d_tmp);
+    cudaFree(p.d_perm);
     npf::split_release(p);
     p.arena.release();
 }
 
 std::atomic<uint64_t> g_next_plan_id{0};
+
+// The caller's modal data (host copies) into the device buffers in the plan's mode order: device
+// mode j is the caller's mode perm[j] (identity without a subset).
+void upload_modes(Plan& p)
+{
+    const int n = p.n;
+    const size_t nn = (size_t)n * n;
+    std::vector<int> perm(n);
+    for (int j = 0; j < n; ++j) perm[j] = p.perm.empty() ? j : p.perm[j];
+    std::vector<double2> U(nn), V(nn), Vt(nn), lam(n);
+    for (int j = 0; j < n; ++j) {
+        lam[j] = p.h_lam[perm[j]];
+        for (int a = 0; a < n; ++a) {
+            U[(size_t)a * n + j] = p.h_U[(size_t)a * n + perm[j]];     // column j = mode perm[j]
+            V[(size_t)j * n + a] = p.h_V[(size_t)perm[j] * n + a];     // row j = mode perm[j]
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) Vt[(size_t)k * n + i] = V[(size_t)i * n + k];
+    NPF_CUDA(cudaMemcpy(p.d_U, U.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
+    NPF_CUDA(cudaMemcpy(p.d_V, V.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
+    NPF_CUDA(cudaMemcpy(p.d_Vt, Vt.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
+    NPF_CUDA(cudaMemcpy(p.d_lam, lam.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+    NPF_CUDA(cudaMemcpy(p.d_perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+}
 
 // Validate (max |V U - I| <= NPF_INVERSE_TOL) and copy the modal data into the plan's buffers.
 void load_modes(Plan& p, const npf_c128* eigvals, const npf_c128* U, const npf_c128* V)
@@ -113,10 +140,11 @@ void load_modes(Plan& p, const npf_c128* eigvals, const npf_c128* U, const npf_c
     if (!(worst <= NPF_INVERSE_TOL))
         npf::fail(NPF_ERR_NOT_INVERSE,
                   "max|V U - I| = " + std::to_string(worst) + " exceeds NPF_INVERSE_TOL");
-    NPF_CUDA(cudaMemcpy(p.d_U, hU.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
-    NPF_CUDA(cudaMemcpy(p.d_V, hV.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
-    NPF_CUDA(cudaMemcpy(p.d_Vt, hVt.data(), nn * sizeof(double2), cudaMemcpyHostToDevice));
-    NPF_CUDA(cudaMemcpy(p.d_lam, eigvals, n * sizeof(double2), cudaMemcpyDefault));
+    p.h_U = std::move(hU);
+    p.h_V = std::move(hV);
+    p.h_lam.resize(n);
+    NPF_CUDA(cudaMemcpy(p.h_lam.data(), eigvals, n * sizeof(double2), cudaMemcpyDefault));
+    upload_modes(p);
 }
 
 
@@ -202,6 +230,11 @@ void compute_npf(Plan& p, int order)
         npf::launch_add(p, p.d_sum, p.d_psiN[m], nn);
     }
     npf::launch_finish(p, order >= 2 ? p.d_sum : nullptr, p.d_npf);
+    if (p.permuted()) {   // modes back to the caller's order
+        npf::launch_unpermute(p, p.d_npf, p.d_tmp, true);
+        NPF_CUDA(cudaMemcpyAsync(p.d_npf, p.d_tmp, (size_t)p.n * p.n * sizeof(double2),
+                                 cudaMemcpyDeviceToDevice, p.stream));
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -468,6 +501,9 @@ npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* 
         NPF_CUDA(cudaMalloc(&p.d_Vt, nn * sizeof(double2)));
         NPF_CUDA(cudaMalloc(&p.d_npf, nn * sizeof(double2)));
         NPF_CUDA(cudaMalloc(&p.d_sum, nn * sizeof(double2)));
+        NPF_CUDA(cudaMalloc(&p.d_tmp, nn * sizeof(double2)));
+        NPF_CUDA(cudaMalloc(&p.d_perm, n * sizeof(int)));
+        p.nm = n;
         for (int N = 2; N <= N_max; ++N) {
             NPF_CUDA(cudaMalloc(&p.d_psiN[N], nn * sizeof(double2)));
             p.packed_count[N] = npf::packed_count(n, N);
@@ -490,6 +526,34 @@ int npf_set_modes(npf_handle* h, const npf_c128* eigvals, const npf_c128* U, con
         NPF_CUDA(cudaStreamSynchronize(p.stream));
         load_modes(p, eigvals, U, V);
         npf::split_refresh_modes(p);   // tensor-core forms: slices of Phi and Psi, in place
+    });
+}
+
+int npf_set_mode_subset(npf_handle* h, int m, const int* modes)
+{
+    return guarded([&] {
+        if (!h) npf::fail(NPF_ERR_ARG, "null handle");
+        Plan& p = h->p;
+        const int n = p.n;
+        if (m < 0 || m > n || (m > 0 && !modes)) npf::fail(NPF_ERR_ARG, "bad mode subset");
+        std::vector<int> perm;
+        if (m > 0 && m < n) {
+            std::vector<int> used(n, 0);
+            for (int j = 0; j < m; ++j) {
+                if (modes[j] < 0 || modes[j] >= n || used[modes[j]])
+                    npf::fail(NPF_ERR_ARG, "subset modes must be distinct and in [0, n)");
+                used[modes[j]] = 1;
+                perm.push_back(modes[j]);
+            }
+            for (int j = 0; j < n; ++j)
+                if (!used[j]) perm.push_back(j);
+        }
+        NPF_CUDA(cudaStreamSynchronize(p.stream));
+        p.perm = perm;
+        p.nm = perm.empty() ? n : m;
+        upload_modes(p);
+        npf::split_refresh_modes(p);
+        ++p.gen;
     });
 }
 
@@ -542,9 +606,18 @@ int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out)
         npf::launch_axpy(p, z, delta, p.d_V, 0.0, nn);
         for (int M = 2; M <= order; ++M)
             if (p.d_tensor[M]) npf::launch_axpy(p, z, std::pow(delta, M), p.d_psiN[M], 1.0, nn);
+        // results leave in the caller's mode order (columns i)
+        auto emit = [&](npf_c128* dst) {
+            const double2* res = p.d_npf;
+            if (p.permuted()) {
+                npf::launch_unpermute(p, p.d_npf, p.d_tmp, true);
+                res = p.d_tmp;
+            }
+            NPF_CUDA(cudaMemcpyAsync(dst, res, nn * sizeof(double2), cudaMemcpyDefault, p.stream));
+        };
         // pN1[k][i] = phi_ki z^i(0)
         npf::launch_hadamard_t(p, 1.0, z, p.d_npf);
-        NPF_CUDA(cudaMemcpyAsync(out, p.d_npf, nn * sizeof(double2), cudaMemcpyDefault, p.stream));
+        emit(out);
         sync(p);
         for (int M = 2; M <= order; ++M) {
             npf_c128* dst = out + (int64_t)(M - 1) * nn;
@@ -556,7 +629,7 @@ int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out)
                 compute_term(p, M, p.d_psiN[M], z);
                 npf::launch_hadamard_t(p, -1.0, p.d_psiN[M], p.d_npf);
             }
-            NPF_CUDA(cudaMemcpyAsync(dst, p.d_npf, nn * sizeof(double2), cudaMemcpyDefault, p.stream));
+            emit(dst);
             sync(p);
         }
     });
@@ -571,7 +644,12 @@ int npf_get_term(npf_handle* h, int order, npf_c128* out)
         if (!p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
         compute_term(p, order, p.d_psiN[order]);
-        NPF_CUDA(cudaMemcpyAsync(out, p.d_psiN[order], (size_t)p.n * p.n * sizeof(double2),
+        const double2* res = p.d_psiN[order];
+        if (p.permuted()) {   // rows i back to the caller's mode order
+            npf::launch_unpermute(p, res, p.d_tmp, false);
+            res = p.d_tmp;
+        }
+        NPF_CUDA(cudaMemcpyAsync(out, res, (size_t)p.n * p.n * sizeof(double2),
                                  cudaMemcpyDefault, p.stream));
         sync(p);
     });
@@ -585,6 +663,8 @@ int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* ou
         if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
         if (!p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
+        if (p.permuted())
+            npf::fail(NPF_ERR_UNSUPPORTED, "modal slabs are not available with a mode subset");
         int pre[npf::kMaxOrder] = {};
         for (int m = 0; m < order - 1; ++m) {
             if (prefix[m] < 0 || prefix[m] >= p.n) npf::fail(NPF_ERR_ARG, "prefix index out of range");

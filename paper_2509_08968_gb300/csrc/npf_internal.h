@@ -99,6 +99,15 @@ struct Plan {
     Arena arena;
     SplitOperand* split = nullptr;
 
+    // critical-mode subset: the device modal data hold the modes in the order perm (the first nm
+    // modes are the subset); the host keeps the caller's modal data in its own order
+    int nm = 0;
+    std::vector<int> perm;
+    int* d_perm = nullptr;
+    double2* d_tmp = nullptr;      // n x n scratch for un-permuting results
+    std::vector<double2> h_lam, h_U, h_V;
+    bool permuted() const { return nm != n || !perm.empty(); }
+
     // batched execution (npf_batch_compute)
     uint64_t id = 0;                // unique over the process, never reused
     uint64_t gen = 0;               // bumped by every change of inputs or options
@@ -139,6 +148,8 @@ void launch_zero(Plan& p, double2* d, int64_t count);
 void launch_add(Plan& p, double2* acc, const double2* x, int64_t count);
 void launch_axpy(Plan& p, double2* y, double a, const double2* x, double b, int64_t count);   // y = a x + b y
 void launch_hadamard_t(Plan& p, double sign, const double2* Z, double2* out);   // out[k][i] = sign U[k][i] Z[i][k]
+// results back to the caller's mode order: columns (out[k][perm[j]] = in[k][j]) or rows
+void launch_unpermute(Plan& p, const double2* in, double2* out, bool columns);
 void build_cnt_table(Plan& p);
 void note_launches(int64_t k);   // k more kernels launched (graph replays)
 
