@@ -176,6 +176,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile-n", type=int, default=0,
                     help="complex columns per tensor-core tile (16/32/64; 0 = library default)")
+    ap.add_argument("--modes", type=int, default=0,
+                    help="critical-mode subset: the m least-damped modes (0 = all modes)")
     ap.add_argument("--workload", default="n120", choices=list(WORKLOADS),
                     help="n120: the measured configuration; the others are small cases for "
                          "profiler captures")
@@ -209,6 +211,11 @@ def main():
                     stream=stream.cuda_stream)
     if args.tile_n:
         plan.set_option(npf.OPT_TILE_N, args.tile_n)
+    subset = None
+    if args.modes and args.modes < n:
+        # least damped first (largest real part), ties by index
+        subset = np.argsort(-sysm.lam.real, kind="stable")[:args.modes]
+        plan.set_mode_subset(subset)
     dev_tensors = {N: torch.from_numpy(sysm.tensors[N]).cuda() for N in ORDERS}
     for N in ORDERS:
         plan.set_tensor(N, dev_tensors[N])
@@ -244,7 +251,9 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     prof = plan.profile(reset=True)
     plan.set_option(npf.OPT_PROFILE, 0)
-    ms, ents = aggregate(dist, ms, entries_per_step(n))
+    m_modes = len(subset) if subset is not None else n
+    ents_rank = sum(m_modes ** (N + 1) for N in ORDERS)   # h^i_p with i, p in the modes used
+    ms, ents = aggregate(dist, ms, ents_rank)
     value = ents / (ms * 1e-3)
 
     # ---- roofline of the dominant kernel (live CUDA-event durations of the timed steps)
@@ -252,7 +261,7 @@ def main():
     roof = None
     if prof:
         name, (cnt, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-        work, kind = algorithmic_work_per_step(name, n, args.precision)
+        work, kind = algorithmic_work_per_step(name, n, args.precision, m_modes)
         if work is not None:
             per_launch = work * args.steps / cnt
             avg_ms = tot_ms / cnt
@@ -291,7 +300,7 @@ def main():
         for _ in range(steps_e2e):
             e2e_step()
         torch.cuda.synchronize()
-        dt, e_all = aggregate(dist, (time.perf_counter() - t0) / steps_e2e, entries_per_step(n))
+        dt, e_all = aggregate(dist, (time.perf_counter() - t0) / steps_e2e, ents_rank)
         e2e = {"value": e_all / dt, "unit": "entries/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
 
@@ -310,7 +319,7 @@ def main():
                                    f"NPF orders {', '.join(map(str, ORDERS))}, packed symmetric "
                                    "tensors 30% N(0,1)",
                        "n": n, "orders": list(ORDERS), "precision": args.precision,
-                       "entries_per_step": entries_per_step(n),
+                       "entries_per_step": ents_rank, "modes": m_modes,
                        "l2": "inputs larger than L2 (packed order-4 tensor 8.7 GB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
@@ -531,7 +540,7 @@ PAIRS = {"split_bf16": 21, "fp32": 6, "fp64": 1}     # BF16 slice pairs s + t < 
 SLICES = {"split_bf16": 6, "fp32": 3, "fp64": 0}
 
 
-def algorithmic_work_per_step(name, n, precision):
+def algorithmic_work_per_step(name, n, precision, m=None):
     """Algorithmic work of every launch of `name` in one step, as (amount, kind).
 
     Tensor kernels (kind "flops"): executed BF16 tensor flops of the work the symmetric method
@@ -548,18 +557,19 @@ def algorithmic_work_per_step(name, n, precision):
     """
     from math import comb
     pairs = PAIRS[precision]
+    m = n if m is None else m          # modes in use (a critical-mode subset); states stay n
     tot = 0
     for N in ORDERS:
         if name == "split_upper_contraction":
-            tot += comb(n + N - 1, N) * n * n * 4 * pairs
+            tot += comb(n + N - 1, N) * m * n * 4 * pairs
         elif name == "split_mode_product":
-            tot += sum(n * comb(n + c - 1, c) * n ** (N - c) * n * 8 for c in range(1, N)) * pairs
+            tot += sum(m * comb(m + c - 1, c) * n ** (N - c) * n * 8 for c in range(1, N)) * pairs
         elif name == "split_mode_divide":
-            tot += n * comb(n + N - 1, N) * n * 8 * pairs
+            tot += m * comb(m + N - 1, N) * n * 8 * pairs
         elif name == "split_reduce":
-            tot += n * comb(n + N - 2, N - 1) * n * n * 8 * pairs
+            tot += m * comb(m + N - 2, N - 1) * n * m * 8 * pairs
         elif name == "split_expand":
-            tot += n * n ** N * (32 + 4 * SLICES[precision])
+            tot += m * n ** N * (32 + 4 * SLICES[precision])
         elif name == "fp64_mode_product":
             tot += (N - 1) * n ** (N + 2) * 8
         else:

@@ -1071,6 +1071,79 @@ __global__ void k_expand(const uint4* __restrict__ rec, int64_t P, int n, int N,
     }
 }
 
+// Next distinct ordering of v[0..len-1] in lexicographic order (false after the last one).
+__device__ __forceinline__ bool next_ordering(int* v, int len)
+{
+    int k = len - 2;
+    while (k >= 0 && v[k] >= v[k + 1]) --k;
+    if (k < 0) return false;
+    int l = len - 1;
+    while (v[l] <= v[k]) --l;
+    const int t = v[k]; v[k] = v[l]; v[l] = t;
+    for (int a = k + 1, b = len - 1; a < b; ++a, --b) { const int u = v[a]; v[a] = v[b]; v[b] = u; }
+    return true;
+}
+
+// Dense expansion by sorted row prefix: one warp per (upper index i, non-decreasing prefix
+// (a_1..a_{N-1}) over [0, n)). Lane t covers a_N = lane + 32 t. The 128 K' digit records
+// S^i_{sort(prefix, a_N)} are gathered once and written to every distinct ordering of the
+// prefix (the dense rows that share them), so a record is read once per prefix rather than once
+// per ordering. Same output as k_expand (rows with an index >= n are not written; K' entries
+// past n are zeros).
+template <int S>
+__global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n, int N, int i0,
+                                int ib, const int64_t* __restrict__ cnt,
+                                const uint32_t* __restrict__ prefixes, int64_t npre,
+                                uint32_t* __restrict__ planes, int64_t plane_stride_u32)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nd = N - 1;
+    int64_t rows_per_i = 1;
+    for (int m = 0; m < nd; ++m) rows_per_i *= NP;
+    for (int64_t item = warp; item < npre * ib; item += nwarps) {
+        const int il = (int)(item / npre);
+        const uint32_t pk = prefixes[item % npre];
+        int pre[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) pre[m] = (int)((pk >> (8 * m)) & 255u);
+        uint32_t w[4][S];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int aN = lane + 32 * t;
+#pragma unroll
+            for (int s = 0; s < S; ++s) w[t][s] = 0u;
+            if (aN < n) {
+                int a[4];
+                int k = 0;
+                bool placed = false;
+                for (int m = 0; m < nd; ++m) {
+                    if (!placed && aN < pre[m]) { a[k++] = aN; placed = true; }
+                    a[k++] = pre[m];
+                }
+                if (!placed) a[k++] = aN;
+                const int64_t q = tuple_rank(a, N, cnt, n);
+                const uint4 r0 = rec[((int64_t)(i0 + il) * P + q) * 2 + 0];
+                const uint4 r1 = rec[((int64_t)(i0 + il) * P + q) * 2 + 1];
+                const uint32_t rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                for (int s = 0; s < S; ++s) w[t][s] = rr[s];
+            }
+        }
+        int ord[3] = {pre[0], pre[1], pre[2]};
+        do {
+            int64_t row = 0;
+            for (int m = 0; m < nd; ++m) row = row * NP + ord[m];
+            uint32_t* dst = planes + ((int64_t)il * rows_per_i + row) * NP + lane;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int s = 0; s < S; ++s) dst[s * plane_stride_u32 + 32 * t] = w[t][s];
+        } while (next_ordering(ord, nd));
+    }
+}
+
 // =======================================================================================
 // Host side
 // =======================================================================================
@@ -1085,6 +1158,8 @@ struct SplitOperand {
     __nv_bfloat16* at[kMaxOrder + 1] = {};
     int* at_e[kMaxOrder + 1] = {};
     int64_t at_rows[kMaxOrder + 1] = {};
+    uint32_t* prefixes[kMaxOrder + 1] = {};   // non-decreasing (a_1..a_{N-1}), 8 bits per index
+    int64_t nprefix[kMaxOrder + 1] = {};
     const double* at_src[kMaxOrder + 1] = {};
     int* err = nullptr;
     // reduction weights other than Psi (mode-interaction NPFs): planes of W^T, exponents, W in
@@ -1212,6 +1287,7 @@ void split_release(Plan& p)
     cudaFree(so->psi_df);
     for (int N = 0; N <= kMaxOrder; ++N) { cudaFree(so->at[N]); cudaFree(so->at_e[N]); }
     cudaFree(so->wred); cudaFree(so->wred_e); cudaFree(so->w_df);
+    for (int N = 0; N <= kMaxOrder; ++N) cudaFree(so->prefixes[N]);
     cudaFree(so->err);
     delete so;
     p.split = nullptr;
@@ -1436,6 +1512,22 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     if (W) prepare_weights(p, so, W);
     set_smem_attrs<S>();
     prepare_tensor<S>(p, so, N);
+    if (!so.prefixes[N]) {   // non-decreasing (N-1)-tuples over [0, n), lexicographic
+        std::vector<uint32_t> pre;
+        std::vector<int> t(N - 1, 0);
+        while (true) {
+            uint32_t pk = 0;
+            for (int m = 0; m < N - 1; ++m) pk |= (uint32_t)t[m] << (8 * m);
+            pre.push_back(pk);
+            int m = N - 2;
+            while (m >= 0 && t[m] == p.n - 1) --m;
+            if (m < 0) break;
+            ++t[m];
+            for (int r = m + 1; r < N - 1; ++r) t[r] = t[m];
+        }
+        so.prefixes[N] = upload(pre);
+        so.nprefix[N] = (int64_t)pre.size();
+    }
     int* const err = p.err_override ? p.err_override : so.err;   // a batch zeroes and checks its own
     if (!p.err_override) NPF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), p.stream));
     const int n = p.n;
@@ -1524,8 +1616,9 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         const int64_t rows = (int64_t)cur * npN1;
         {
             LaunchScope ls(&p.prof, "split_expand", p.stream);
-            k_expand<S><<<8192, 256, 0, p.stream>>>(rec, P, n, N, i0, cur, p.d_cnt,
-                                                    (uint32_t*)T[0], t_rows * (KP / 2));
+            k_expand_sorted<S><<<8192, 256, 0, p.stream>>>(rec, P, n, N, i0, cur, p.d_cnt,
+                                                           so.prefixes[N], so.nprefix[N],
+                                                           (uint32_t*)T[0], t_rows * (KP / 2));
             NPF_CUDA(cudaGetLastError());
         }
         int cb = 0;
