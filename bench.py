@@ -385,7 +385,7 @@ def run_batch(args, world, rank, local, dist):
     for s, N in systems:
         n = s.n
         f = n * comb(n + N - 1, N) * n * 4
-        f += sum(n * comb(n + c - 1, c) * n ** (N - c) * n * 8 for c in range(1, N))
+        f += sum(n * comb(n + c - 1, c) * a_part(n, N, c) * n * 8 for c in range(1, N))
         f += n * comb(n + N - 1, N) * n * 8 + n * comb(n + N - 2, N - 1) * n * n * 8
         f *= pairs
         t = args.tile_n or npf.tuned_tile(n, N, args.precision) or 64
@@ -540,6 +540,14 @@ PAIRS = {"split_bf16": 21, "fp32": 6, "fp64": 1}     # BF16 slice pairs s + t < 
 SLICES = {"split_bf16": 6, "fp32": 3, "fp64": 0}
 
 
+def a_part(n, N, c):
+    """Lower-input index tuples (a's) formed by contraction c: the innermost a is dense, shared
+    a's are dense too except a pair of them, which is formed non-decreasing."""
+    from math import comb
+    sa = N - c - 1
+    return (comb(n + 1, 2) if sa == 2 else n ** sa) * n
+
+
 def algorithmic_work_per_step(name, n, precision, m=None):
     """Algorithmic work of every launch of `name` in one step, as (amount, kind).
 
@@ -548,8 +556,9 @@ def algorithmic_work_per_step(name, n, precision, m=None):
     a complex multiply-add over K is 8 real flops, times the slice pairs. Per order N with
     C(m, r) = binomial:
       split_upper_contraction : C(n+N-1,N) packed tuples x n (i) x n (j) x 4 (real x complex)
-      split_mode_product      : sum_{c=1..N-1} n (i) x C(n+c-1,c) (sorted p's) x n^(N-c) (a's)
-                                x n (K) x 8
+      split_mode_product      : sum_{c=1..N-1} n (i) x C(n+c-1,c) (sorted p's) x A_c (a's)
+                                x n (K) x 8, A_c = n^(N-c), except that two shared a's are
+                                formed non-decreasing only: A_c = C(n+1,2) n when N-c-1 = 2
       split_mode_divide       : n (i) x C(n+N-1,N) x n (K) x 8
       split_reduce            : n (i) x C(n+N-2,N-1) (rows) x n (k) x n (K) x 8
     Memory kernels (kind "bytes"): split_expand gathers one 32-byte digit record and writes
@@ -563,7 +572,7 @@ def algorithmic_work_per_step(name, n, precision, m=None):
         if name == "split_upper_contraction":
             tot += comb(n + N - 1, N) * m * n * 4 * pairs
         elif name == "split_mode_product":
-            tot += sum(m * comb(m + c - 1, c) * n ** (N - c) * n * 8 for c in range(1, N)) * pairs
+            tot += sum(m * comb(m + c - 1, c) * a_part(n, N, c) * n * 8 for c in range(1, N)) * pairs
         elif name == "split_mode_divide":
             tot += m * comb(m + N - 1, N) * n * 8 * pairs
         elif name == "split_reduce":

@@ -363,6 +363,9 @@ struct RowArgs {
     int digits;          // 1: r carries N-1 index digits (0 for the packed-tuple rows of P1)
     int rp;              // leading p digits in r
     int colmask;         // new column must be <= the first p
+    int aswap;           // EPI_SLICE: only tiles with non-decreasing shared a's run, and each
+                         // output row is also written for the swapped pair of shared a's
+                         // (orders <= 4 have at most two shared a's)
     int64_t R;           // rows per outer index (output layout [outer][q][r])
     int npc;             // extent of the new index in the output layout
     int n;               // states (range of the a digits and of the reduction's columns k)
@@ -419,6 +422,9 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_loca
         if (m + 1 >= nd) break;                            // shared digits: 0 .. nd-2
         if (d[m] >= (m < a.rp ? a.nm : a.n)) return true;  // padding index: rows are zero
         if (m >= 1 && m < a.rp && d[m - 1] > d[m]) return true;
+        // shared a's: the output is symmetric in them, so only non-decreasing ones are formed
+        // and the epilogue writes each row to every ordering (aswap)
+        if (a.aswap && m > a.rp && d[m - 1] > d[m]) return true;
     }
     const bool first_shared = a.rp >= 1 && nd >= 2;
     if (a.colmask && first_shared && ct * a.bnc > d[0]) return true;
@@ -633,6 +639,16 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 if (args.rp >= 1) firstp = dg[0];
             }
 
+            // rows of the swapped pair of shared a's (digits rp, rp + 1 when both are shared):
+            // offset of that row in the output's row index (shared digits, base NP)
+            int64_t swap_off = 0;
+            if (MODE == EPI_SLICE && args.aswap) {
+                const int j = args.rp, nd = N - 1;
+                if (j + 1 <= nd - 2 && dg[j] < dg[j + 1]) {
+                    const int64_t wj = ipow_np(nd - 2 - j), wj1 = ipow_np(nd - 3 - j);
+                    swap_off = (int64_t)(dg[j + 1] - dg[j]) * wj + (int64_t)(dg[j] - dg[j + 1]) * wj1;
+                }
+            }
             // per-tile tables: column exponents, the fixed matrix's column exponents, lambda_q
             // (FP32 and as exact triple-floats); per row (one thread of each row): sigma of the
             // row p's minus lambda_i, the multiplicity base and the first run length
@@ -937,6 +953,12 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 #pragma unroll
                         for (int s = 0; s < S; ++s) dst[s * (args.out_plane_stride / 2)] = w[s];
                         if (rl == 0) args.out_exp[rowp] = E;
+                        if (MODE == EPI_SLICE && swap_off != 0) {   // the same row, shared a's swapped
+                            uint32_t* d2 = dst + swap_off * (KP / 2);
+#pragma unroll
+                            for (int s = 0; s < S; ++s) d2[s * (args.out_plane_stride / 2)] = w[s];
+                            if (rl == 0) args.out_exp[rowp + swap_off] = E;
+                        }
                     }
                 }
             }
@@ -1133,6 +1155,10 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
         }
         int ord[3] = {pre[0], pre[1], pre[2]};
         do {
+            // the first contraction only runs rows whose shared indices are non-decreasing
+            bool sorted_shared = true;
+            for (int m = 1; m < nd - 1; ++m) sorted_shared &= ord[m - 1] <= ord[m];
+            if (!sorted_shared) continue;
             int64_t row = 0;
             for (int m = 0; m < nd; ++m) row = row * NP + ord[m];
             uint32_t* dst = planes + ((int64_t)il * rows_per_i + row) * NP + lane;
@@ -1634,6 +1660,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
             a.digits = 1;
             a.rp = c - 1;              // p_{N-c+2}..p_N lead the row, then a_1..a_{N-c}
             a.colmask = c >= 2;        // new index p_{N-c+1} <= p_{N-c+2}
+            a.aswap = c < N;           // mode products: shared a's non-decreasing, rows mirrored
             a.R = npN1;
             a.npc = NP;
             a.i0 = i0;
