@@ -78,13 +78,17 @@ enum npf_option {
                                0 = autotuned: the first term of each (n, order, precision,
                                slices, divide) times every width on the plan's own work and the
                                fastest is kept for the process (npf_tuned_tile). */
-    NPF_OPT_FP64_QUOTIENT = 8 /* tensor-core forms, Alg. 2 steps 5-11: 1 = form h = C / D with
+    NPF_OPT_FP64_QUOTIENT = 8, /* tensor-core forms, Alg. 2 steps 5-11: 1 = form h = C / D with
                                native FP64 arithmetic; 0 (default) = the denominator
                                D = lambda_p1 + .. + lambda_pN - lambda_i exactly from FP64 inputs
                                (error-free float transformations, exact under cancellation) and
                                the quotient in double-float arithmetic (relative error ~2^-45),
                                about 5x faster on this GPU, whose FP64 rate is ~1/900 of its
                                tensor rate. Both are rounded to the same 6 x 8-bit slices next. */
+    NPF_OPT_DEBUG_STALL = 9   /* test hook (not for use): 1 makes the tensor-core pipeline withhold
+                               its first completion signal, so a bounded device wait runs out
+                               (about 2 s) and the call returns NPF_ERR_TIMEOUT with the CUDA
+                               context intact. */
 };
 
 /* Arithmetic of the dense contraction. The denominators, the divide, the Psi_N sums and the

@@ -27,7 +27,7 @@ NPF_ERR_TIMEOUT = 6
 NPF_ERR_UNSUPPORTED = 7
 
 (OPT_PRECISION, OPT_EPS, OPT_STREAM, OPT_SLICES, OPT_DIVIDE, OPT_MEM_BUDGET, OPT_PROFILE,
- OPT_TILE_N, OPT_FP64_QUOTIENT) = range(9)
+ OPT_TILE_N, OPT_FP64_QUOTIENT, OPT_DEBUG_STALL) = range(10)
 PREC_FP64, PREC_SPLIT_BF16, PREC_FP32 = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "split_bf16": PREC_SPLIT_BF16, "fp32": PREC_FP32}
 

@@ -384,6 +384,8 @@ struct RowArgs {
     double invfact, eps;
     int divide;
     int fp64_quotient;   // EPI_DIVIDE: native FP64 quotient instead of the double-float one
+    int stall;           // test hook: the MMA role never signals the first tile's accumulators,
+                         // so the epilogue's bounded wait runs out (timeout path)
     float eps2f;         // eps^2 in FP32 (clamp test of the double-float quotient)
     int pre[8];          // EPI_SLAB: the requested prefix (N-1 indices)
     int* err;
@@ -431,11 +433,14 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_loca
     return false;
 }
 
-// Wait with a fixed spin limit and no early exit (draining copies after an error).
+// Wait with the same limits and no early exit (draining copies after an error).
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
 {
-    for (long long it = 0; it < tc::kWaitLimit; ++it)
+    const unsigned long long t0 = tc::wall_ns();
+    for (long long it = 0; it < tc::kWaitLimit; ++it) {
         if (tc::mbar_try_wait(bar, parity)) return;
+        if ((it & 1023) == 1023 && tc::wall_ns() - t0 > tc::kWaitNs) return;
+    }
 }
 
 // One K' chunk of MMAs: every slice pair (s, u) with s + u < S into its level accumulator, NKS
@@ -595,7 +600,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     tc::mma_commit(&empty[st]);
                 }
                 if (!alive) break;
-                tc::mma_commit(tfull);
+                if (!args.stall) tc::mma_commit(tfull);
                 ++t;
             }
         }
@@ -1606,6 +1611,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     base0.eps = p.eps;
     base0.divide = p.divide;
     base0.fp64_quotient = p.fp64_quotient;
+    base0.stall = p.debug_stall;
     base0.eps2f = (float)(p.eps * p.eps);
     base0.err = err;
     base0.bnc = p.tile_n;

@@ -9,8 +9,17 @@
 namespace npf {
 namespace tc {
 
-// Spin limit of every bounded wait (try_wait itself suspends for a while between polls).
+// Limits of every bounded wait: a poll count and a wall-clock budget (try_wait itself suspends
+// for a while between polls, so the time limit is the one that normally ends a stuck wait).
 constexpr long long kWaitLimit = 1ll << 26;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long wall_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -45,14 +54,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity to complete; gives up after kWaitLimit polls (or as
-// soon as another role of the kernel has recorded an error), records `code` in *err and returns
-// false.
+// Wait for the phase with the given parity to complete; gives up after kWaitNs (or kWaitLimit
+// polls), records `code` in *err and returns false; returns false at once when another role of
+// the kernel has recorded an error.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code)
 {
+    const unsigned long long t0 = wall_ns();
     for (long long it = 0; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 1023) == 1023 && *(volatile int*)err) return false;
+        if ((it & 1023) == 1023) {
+            if (*(volatile int*)err) return false;
+            if (wall_ns() - t0 > kWaitNs) break;
+        }
     }
     atomicCAS(err, 0, code);
     return false;

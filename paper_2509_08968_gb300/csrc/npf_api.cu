@@ -737,6 +737,9 @@ int npf_set_option(npf_handle* h, int key, double value)
         case NPF_OPT_FP64_QUOTIENT:
             p.fp64_quotient = value != 0.0;
             break;
+        case NPF_OPT_DEBUG_STALL:
+            p.debug_stall = value != 0.0;
+            break;
         default:
             npf::fail(NPF_ERR_ARG, "unknown option key");
         }

@@ -75,6 +75,7 @@ struct Plan {
     double eps = 1e-8;
     int divide = 1;
     int fp64_quotient = 0;         // tensor-core divide epilogue: 1 = native FP64 quotient
+    int debug_stall = 0;           // test hook of the timeout path (NPF_OPT_DEBUG_STALL)
     int tile_n = 64;               // complex columns per tensor-core tile; 0 = autotuned
     size_t mem_budget = 0;         // 0 = 80% of free memory at compute time
     cudaStream_t stream = nullptr;
