@@ -386,7 +386,7 @@ def run_batch(args, world, rank, local, dist):
         n = s.n
         f = n * comb(n + N - 1, N) * n * 4
         f += sum(n * comb(n + c - 1, c) * a_part(n, N, c) * n * 8 for c in range(1, N))
-        f += n * comb(n + N - 1, N) * n * 8 + n * comb(n + N - 2, N - 1) * n * n * 8
+        f += n * comb(n + N - 1, N) * n * 8 + n * comb(n + N - 1, N) * n * 8
         f *= pairs
         t = args.tile_n or npf.tuned_tile(n, N, args.precision) or 64
         tiles[f"n{n}o{N}"] = t
@@ -560,7 +560,7 @@ def algorithmic_work_per_step(name, n, precision, m=None):
                                 x n (K) x 8, A_c = n^(N-c), except that two shared a's are
                                 formed non-decreasing only: A_c = C(n+1,2) n when N-c-1 = 2
       split_mode_divide       : n (i) x C(n+N-1,N) x n (K) x 8
-      split_reduce            : n (i) x C(n+N-2,N-1) (rows) x n (k) x n (K) x 8
+      split_reduce            : n (i) x C(n+N-1,N) (sorted rows x p_N >= p_{N-1}) x n (k) x 8
     Memory kernels (kind "bytes"): split_expand gathers one 32-byte digit record and writes
     S planes x 4 bytes per dense operand entry: n (i) x n^N x (32 + 4 S).
     """
@@ -576,7 +576,7 @@ def algorithmic_work_per_step(name, n, precision, m=None):
         elif name == "split_mode_divide":
             tot += m * comb(m + N - 1, N) * n * 8 * pairs
         elif name == "split_reduce":
-            tot += m * comb(m + N - 2, N - 1) * n * m * 8 * pairs
+            tot += m * comb(m + N - 1, N) * n * 8 * pairs
         elif name == "split_expand":
             tot += m * n ** N * (32 + 4 * SLICES[precision])
         elif name == "fp64_mode_product":
