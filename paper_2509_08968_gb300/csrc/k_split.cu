@@ -363,6 +363,7 @@ struct RowArgs {
     int digits;          // 1: r carries N-1 index digits (0 for the packed-tuple rows of P1)
     int rp;              // leading p digits in r
     int colmask;         // new column must be <= the first p
+    int kfrom;           // EPI_REDUCE: skip the K' chunks below the tile's last shared p
     int aswap;           // EPI_SLICE: only tiles with non-decreasing shared a's run, and each
                          // output row is also written for the swapped pair of shared a's
                          // (orders <= 4 have at most two shared a's)
@@ -431,6 +432,21 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_loca
     const bool first_shared = a.rp >= 1 && nd >= 2;
     if (a.colmask && first_shared && ct * a.bnc > d[0]) return true;
     return false;
+}
+
+// First K' chunk a tile needs. In the reduction (kfrom = 1) the rows are (i, p_1..p_{N-1}) and
+// K = p_N; only non-decreasing tuples are formed, so every valid row of a tile has
+// p_N >= p_{N-1} >= p_{N-2} (its last shared digit) and the chunks below p_{N-2} are zero.
+__device__ __forceinline__ int first_chunk(const RowArgs& a, int64_t row0_local)
+{
+    if (!a.kfrom || a.N < 3) return 0;
+    int d[8];
+    row_digits(row0_local % a.R, a.N - 1, d);
+    int kmin = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        if (m == a.N - 3) kmin = d[m];
+    return kmin / 16;   // 16 complex K entries per chunk of 32 K'
 }
 
 // Wait with the same limits and no early exit (draining copies after an error).
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const int64_t row0 = tile / ncol * NP;
                 if (tile_skipped(args, row0, ct)) continue;
                 const int bc = ct * bnc;
-                for (int kc = 0; kc < args.kch; ++kc, ++it) {
+                for (int kc = first_chunk(args, row0); kc < args.kch; ++kc, ++it) {
                     const int st = (int)(it % C::STAGES);
                     const uint32_t ph = (it / C::STAGES) & 1;
                     if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) {
@@ -578,7 +594,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 if (tile_skipped(args, row0, ct)) continue;
                 if (!tc::mbar_wait(tempty, (t & 1) ^ 1, args.err, kErrTimeout)) break;
                 tc::fence_after_sync();
-                for (int kc = 0; kc < args.kch; ++kc, ++it) {
+                const int kc0 = first_chunk(args, row0);
+                for (int kc = kc0; kc < args.kch; ++kc, ++it) {
                     const int st = (int)(it % C::STAGES);
                     const uint32_t ph = (it / C::STAGES) & 1;
                     if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) {
@@ -590,7 +607,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     const uint32_t a_lo = tc::sdesc_sw64_lo(aBase);
                     const uint32_t b_lo = tc::sdesc_sw64_lo(aBase + S * C::A_TILE);
                     const bool half = kc == args.kch - 1 && args.klast == 1;
-                    if (kc == 0) {
+                    if (kc == kc0) {
                         if (half) issue_chunk<S, true, 1>(tmem, a_lo, b_lo, idesc);
                         else issue_chunk<S, true, 2>(tmem, a_lo, b_lo, idesc);
                     } else {
@@ -1690,6 +1707,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         a.kch = (2 * nm + BK - 1) / BK;   // K' = 2 p_N + re/im < 2 nm
         a.klast = (2 * nm + 15) / 16 - 2 * (a.kch - 1);
         a.ncv = n;                         // columns: states k
+        a.kfrom = 1;                       // K = p_N >= the tile's last shared p
         a.ea = E[cb];
         a.ea_shift = 0;
         a.eb = W ? so.wred_e : so.red_e;
