@@ -91,8 +91,10 @@ enum npf_option {
                                context intact. */
 };
 
-/* Arithmetic of the dense contraction. The denominators, the divide, the Psi_N sums and the
- * NPF finish are native FP64 in every form. */
+/* Arithmetic of the dense contraction. In every form the resonance denominators are formed
+ * exactly from the FP64 eigenvalues and the Psi_N sums and the NPF finish are FP64; the quotient
+ * h = C / D is native FP64 in the FP64 form and double-float in the tensor-core forms (native FP64
+ * with NPF_OPT_FP64_QUOTIENT). */
 enum npf_precision {
     NPF_PREC_FP64 = 0,        /* native FP64 (CUDA-core DFMA) contraction */
     NPF_PREC_SPLIT_BF16 = 1,  /* FP64-emulating BF16 slices on tcgen05 tensor cores, FP32
@@ -114,7 +116,7 @@ npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* 
  * the paper: for sweeps over operating points of one model. */
 int npf_set_modes(npf_handle* h, const npf_c128* eigvals, const npf_c128* U, const npf_c128* V);
 
-/* Critical-mode subset (the reduction suggested in Section III): with m > 0 the modal indices
+/* Critical-mode subset (the reduction the paper suggests in Section III, numerical experiment): with m > 0 the modal indices
  * i, p_1..p_N of Eq. 4 and the sums of Eq. 7 run over the m listed modes only (modes[m],
  * distinct, in [0, n)); the states and the tensor are unchanged, so the work drops from
  * ~n^(N+2) to ~n m^(N+1). NPF columns (modes) outside the subset then carry the linear PF only,
