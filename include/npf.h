@@ -152,6 +152,13 @@ int npf_get_term(npf_handle* h, int order, npf_c128* out);
  * out: [order][n][n], host or device. The plan's Psi_M terms and NPF buffer are overwritten. */
 int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out);
 
+/* Rows i_lo <= i < i_hi of Psi_N (out[i*n + k], the other rows zero; host or device): the upper
+ * index is independent across rows (Eq. 7 sums over the lower indices only), so disjoint row
+ * ranges computed separately -- on several GPUs, or resumed after an interruption -- add up to
+ * npf_get_term. The tensor-core forms only form those rows; the FP64 form runs its mode
+ * products in full and reduces only those rows. Not available with a mode subset. */
+int npf_get_term_rows(npf_handle* h, int order, int i_lo, int i_hi, npf_c128* out);
+
 /* One modal slab h^i_{prefix, q}: out[i*n + q] for the fixed prefix p_1..p_{N-1} (N-1 ints in
  * [0, n)), every mode i and last index q. Host or device `out`. For parity checks at full size. */
 int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* out);

@@ -74,6 +74,7 @@ def load():
     lib.npf_get_term.argtypes = [vp, ci, vp]
     lib.npf_get_modal_slab.argtypes = [vp, ci, vp, vp]
     lib.npf_interaction.argtypes = [vp, ci, cd, vp]
+    lib.npf_get_term_rows.argtypes = [vp, ci, ci, ci, vp]
     lib.npf_batch_compute.argtypes = [ci, vp, vp, vp]
     lib.npf_last_error.restype = ctypes.c_char_p
     lib.npf_last_status.restype = ci
@@ -187,6 +188,13 @@ class Plan:
         if out is None:
             out = np.empty((order, self.n, self.n), dtype=np.complex128)
         _check(load().npf_interaction(self._h, order, float(delta), _ptr(out)))
+        return out
+
+    def term_rows(self, order, i_lo, i_hi, out=None):
+        """Rows [i_lo, i_hi) of Psi_N (other rows zero)."""
+        if out is None:
+            out = np.empty((self.n, self.n), dtype=np.complex128)
+        _check(load().npf_get_term_rows(self._h, order, int(i_lo), int(i_hi), _ptr(out)))
         return out
 
     def modal_slab(self, order, prefix, out=None):

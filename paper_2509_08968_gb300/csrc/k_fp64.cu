@@ -242,8 +242,9 @@ void fp64_term(Plan& p, int N, double2* d_out, const double2* W)
         // then N-1 diagonal contractions over p_{N-1}, .., p_1 alternate between Y and bufC,
         // the last one subtracting into rows i0.. of d_out.
         const int64_t nN1 = nN / n;
-        for (int i0 = 0; i0 < n; i0 += nb) {
-            const int c = std::min(nb, n - i0);
+        const int rlo = std::max(0, p.row_lo), rhi = p.row_hi < 0 ? n : std::min(p.row_hi, n);
+        for (int i0 = rlo; i0 < rhi; i0 += nb) {
+            const int c = std::min(nb, rhi - i0);
             gemm(p, "fp64_reduce_gemm", X + (int64_t)i0 * nN1 * cur, (int64_t)c * nN1, cur,
                  Wr + (int64_t)b0 * n, n, n, Y, 1, none);
             double2* src = Y;

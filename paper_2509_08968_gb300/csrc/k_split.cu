@@ -1660,8 +1660,10 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         NPF_CUDA(cudaGetLastError());
     }
 
-    for (int i0 = 0; i0 < nm; i0 += ib) {
-        const int cur = std::min(ib, nm - i0);
+    const int rlo = std::max(0, p.row_lo);                       // upper-index rows to form
+    const int rhi = p.row_hi < 0 ? nm : std::min(p.row_hi, nm);
+    for (int i0 = rlo; i0 < rhi; i0 += ib) {
+        const int cur = std::min(ib, rhi - i0);
         const int64_t rows = (int64_t)cur * npN1;
         {
             LaunchScope ls(&p.prof, "split_expand", p.stream);

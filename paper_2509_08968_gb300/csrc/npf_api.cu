@@ -635,6 +635,34 @@ int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out)
     });
 }
 
+int npf_get_term_rows(npf_handle* h, int order, int i_lo, int i_hi, npf_c128* out)
+{
+    return guarded([&] {
+        if (!h || !out) npf::fail(NPF_ERR_ARG, "null handle or out");
+        Plan& p = h->p;
+        if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        if (i_lo < 0 || i_hi > p.n || i_lo >= i_hi) npf::fail(NPF_ERR_ARG, "bad row range");
+        if (!p.d_tensor[order])
+            npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
+        if (p.permuted())
+            npf::fail(NPF_ERR_UNSUPPORTED, "row ranges are not available with a mode subset");
+        p.row_lo = i_lo;
+        p.row_hi = i_hi;
+        try {
+            compute_term(p, order, p.d_psiN[order]);
+        } catch (...) {
+            p.row_lo = 0;
+            p.row_hi = -1;
+            throw;
+        }
+        p.row_lo = 0;
+        p.row_hi = -1;
+        NPF_CUDA(cudaMemcpyAsync(out, p.d_psiN[order], (size_t)p.n * p.n * sizeof(double2),
+                                 cudaMemcpyDefault, p.stream));
+        sync(p);
+    });
+}
+
 int npf_get_term(npf_handle* h, int order, npf_c128* out)
 {
     return guarded([&] {
