@@ -30,7 +30,7 @@ N_STATES = 120
 ORDERS = (3, 4)
 # name -> (n, orders)
 WORKLOADS = {"n120": (120, (3, 4)), "n60": (60, (3, 4)), "n120o3": (120, (3,)),
-             "batch256": (None, (2, 3)), "surrogate": (40, (2, 3))}
+             "batch256": (None, (2, 3)), "surrogate": (40, (2, 3)), "swing120": (120, (3, 4))}
 METRIC = "modal-tensor entries/s & % roofline, split-prec vs native FP64 at rel err <=1e-10"
 
 
@@ -204,7 +204,12 @@ def main():
 
     global N_STATES, ORDERS
     N_STATES, ORDERS = WORKLOADS[args.workload]
-    sysm = S.config_blocks(N_STATES, rank, orders=ORDERS)
+    swing = args.workload.startswith("swing")
+    if swing:   # tensors generated on the GPU from a 60-machine swing model
+        model = S.swing_model(N_STATES // 2, rank)
+        sysm = S.swing_system(model)
+    else:
+        sysm = S.config_blocks(N_STATES, rank, orders=ORDERS)
     n = sysm.n
     stream = torch.cuda.current_stream()
     plan = npf.Plan(sysm.lam, sysm.U, sysm.V, max(ORDERS), precision=args.precision,
@@ -216,9 +221,13 @@ def main():
         # least damped first (largest real part), ties by index
         subset = np.argsort(-sysm.lam.real, kind="stable")[:args.modes]
         plan.set_mode_subset(subset)
-    dev_tensors = {N: torch.from_numpy(sysm.tensors[N]).cuda() for N in ORDERS}
-    for N in ORDERS:
-        plan.set_tensor(N, dev_tensors[N])
+    if swing:
+        for N in ORDERS:
+            plan.set_tensor_swing(N, model)
+    else:
+        dev_tensors = {N: torch.from_numpy(sysm.tensors[N]).cuda() for N in ORDERS}
+        for N in ORDERS:
+            plan.set_tensor(N, dev_tensors[N])
     out = torch.empty((n, n), dtype=torch.complex128, device="cuda")
 
     def step():
@@ -281,15 +290,23 @@ def main():
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        host_t = {N: torch.from_numpy(sysm.tensors[N]).pin_memory() for N in ORDERS}
         host_out = torch.empty((n, n), dtype=torch.complex128).pin_memory()
-        h2d = sum(int(t.numel() * 8) for t in host_t.values())
         d2h = int(host_out.numel() * 16)
+        if swing:   # the step's inputs are the model parameters; tensors generated on the GPU
+            h2d = 8 * (3 * model.m + 2 * model.m * model.m) * len(ORDERS)
 
-        def e2e_step():
-            for N in ORDERS:
-                plan.set_tensor(N, host_t[N])
-            plan.compute(max(ORDERS), host_out)
+            def e2e_step():
+                for N in ORDERS:
+                    plan.set_tensor_swing(N, model)
+                plan.compute(max(ORDERS), host_out)
+        else:
+            host_t = {N: torch.from_numpy(sysm.tensors[N]).pin_memory() for N in ORDERS}
+            h2d = sum(int(t.numel() * 8) for t in host_t.values())
+
+            def e2e_step():
+                for N in ORDERS:
+                    plan.set_tensor(N, host_t[N])
+                plan.compute(max(ORDERS), host_out)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -315,9 +332,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"n={n} block-structured system ({n // 4} blocks x 4 states), "
-                                   f"NPF orders {', '.join(map(str, ORDERS))}, packed symmetric "
-                                   "tensors 30% N(0,1)",
+            "config": {"workload": (f"n={n} swing model ({n // 2} machines, ring + random lines), "
+                                    f"NPF orders {', '.join(map(str, ORDERS))}, derivative tensors "
+                                    "generated on the GPU") if swing else
+                                   (f"n={n} block-structured system ({n // 4} blocks x 4 states), "
+                                    f"NPF orders {', '.join(map(str, ORDERS))}, packed symmetric "
+                                    "tensors 30% N(0,1)"),
                        "n": n, "orders": list(ORDERS), "precision": args.precision,
                        "entries_per_step": ents_rank, "modes": m_modes,
                        "l2": "inputs larger than L2 (packed order-4 tensor 8.7 GB)"},

@@ -129,6 +129,24 @@ int npf_set_mode_subset(npf_handle* h, int m, const int* modes);
  * the plan's device memory. Replaces a previous tensor of that order. */
 int npf_set_tensor(npf_handle* h, int order, const double* coeffs);
 
+/* The order-`order` derivative tensor of a multi-machine swing model, generated on the GPU into
+ * the plan (the numerical Taylor step that Algorithm 1 batches, Section II.B, in closed form; no
+ * host copy of the n x C(n+N-1, N) coefficients). n = 2m states (delta_0..delta_{m-1},
+ * omega_0..omega_{m-1}) with d delta_j/dt = omega_j and
+ * d omega_j/dt = (P_j - D_j omega_j - sum_k V_j V_k (G_jk cos(delta_j - delta_k)
+ *                 + B_jk sin(delta_j - delta_k)) - V_j (Gb_j cos delta_j + Bb_j sin delta_j))
+ *                / (2 H_j)
+ * (the last term: a line to a reference bus of voltage 1 and angle 0), expanded at the angles
+ * delta[m]: H[m], V[m], delta[m], G[m*m], B[m*m] (row-major), Gb[m], Bb[m] (NULL = no reference
+ * lines); host or device. P and D do not enter orders >= 2. Replaces the order's tensor as
+ * npf_set_tensor does. */
+int npf_set_tensor_swing(npf_handle* h, int order, const double* H, const double* V,
+                         const double* delta, const double* G, const double* B, const double* Gb,
+                         const double* Bb);
+
+/* The plan's packed order-`order` tensor into out[n*P] (host or device). */
+int npf_get_tensor(npf_handle* h, int order, double* out);
+
 /* NPF of the given order (1..N_max) into out[n*n] (host or device): linear PFs plus Psi_m of
  * every order 2..order that has a tensor set (each order is an independent approximation, Eq. 4).
  * Returns NPF_ERR_MISSING_TENSOR only when order >= 2 and that order's own tensor is missing. */

@@ -256,3 +256,92 @@ def operating_points(fam: OperatingPointFamily, count: int, seed: int) -> np.nda
     """`count` parameter vectors drawn uniformly from the family's box, [count, 4]."""
     rng = np.random.default_rng(seed)
     return fam.lo + (fam.hi - fam.lo) * rng.random((count, 4))
+
+
+# ----------------------------------------------------------------------------------------
+# Multi-machine swing model (power-system-shaped inputs with closed-form derivatives).
+# ----------------------------------------------------------------------------------------
+
+@dataclass
+class SwingModel:
+    """m machines, states x = (delta_0..delta_{m-1}, omega_0..omega_{m-1}):
+    d delta_j/dt = omega_j,
+    d omega_j/dt = (P_j - D_j omega_j - sum_k V_j V_k (G_jk cos(d_j - d_k) + B_jk sin(d_j - d_k)))
+                   / (2 H_j),
+    with P_j chosen so that the angles `delta` (and omega = 0) are an equilibrium."""
+    m: int
+    H: np.ndarray
+    D: np.ndarray
+    V: np.ndarray
+    delta: np.ndarray
+    G: np.ndarray      # [m, m], symmetric, zero diagonal
+    B: np.ndarray      # [m, m], symmetric, zero diagonal
+    P: np.ndarray
+    Gb: np.ndarray     # [m] lines to a reference bus (voltage 1, angle 0)
+    Bb: np.ndarray
+
+    def f(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        m = self.m
+        d, w = x[:m], x[m:]
+        t = d[:, None] - d[None, :]
+        net = (self.V[:, None] * self.V[None, :] * (self.G * np.cos(t) + self.B * np.sin(t))).sum(1)
+        net = net + self.V * (self.Gb * np.cos(d) + self.Bb * np.sin(d))
+        return np.concatenate([w, (self.P - self.D * w - net) / (2.0 * self.H)])
+
+    def jacobian(self):
+        """A1 at the equilibrium (closed form)."""
+        m = self.m
+        t = self.delta[:, None] - self.delta[None, :]
+        gp = self.V[:, None] * self.V[None, :] * (-self.G * np.sin(t) + self.B * np.cos(t))
+        np.fill_diagonal(gp, 0.0)
+        bus = self.V * (-self.Gb * np.sin(self.delta) + self.Bb * np.cos(self.delta))
+        A = np.zeros((2 * m, 2 * m))
+        A[:m, m:] = np.eye(m)
+        A[m:, :m] = (gp - np.diag(gp.sum(1) + bus)) / (2.0 * self.H)[:, None]
+        A[m:, m:] = -np.diag(self.D / (2.0 * self.H))
+        return A
+
+
+def swing_model(m: int, seed: int = 0, bus: bool = True) -> SwingModel:
+    """A ring of m machines plus random extra lines (about two per machine); line susceptances
+    U[5, 15], conductances U[0, 1]; inertia H ~ U[2, 8], damping D ~ U[0.5, 2], voltages
+    U[0.95, 1.05], angles N(0, 0.2); with `bus`, every third machine also has a line to a
+    reference bus (susceptance U[5, 15], conductance U[0, 1]), which removes the rotational zero
+    mode (without it the modes include lambda = 0 and the denominators lambda_0 + lambda_p -
+    lambda_p vanish exactly)."""
+    rng = np.random.default_rng(seed + 911)
+    B = np.zeros((m, m))
+    G = np.zeros((m, m))
+    edges = {(j, (j + 1) % m) for j in range(m)} if m > 2 else {(0, 1)}
+    for _ in range(2 * m):
+        a, b = rng.integers(0, m, 2)
+        if a != b:
+            edges.add((min(a, b), max(a, b)))
+    for a, b in edges:
+        a, b = min(a, b), max(a, b)
+        B[a, b] = B[b, a] = rng.uniform(5.0, 15.0)
+        G[a, b] = G[b, a] = rng.uniform(0.0, 1.0)
+    H = rng.uniform(2.0, 8.0, m)
+    D = rng.uniform(0.5, 2.0, m)
+    V = rng.uniform(0.95, 1.05, m)
+    delta = rng.normal(0.0, 0.2, m)
+    Gb = np.zeros(m)
+    Bb = np.zeros(m)
+    if bus:
+        for j in range(0, m, 3):
+            Bb[j] = rng.uniform(5.0, 15.0)
+            Gb[j] = rng.uniform(0.0, 1.0)
+    t = delta[:, None] - delta[None, :]
+    P = (V[:, None] * V[None, :] * (G * np.cos(t) + B * np.sin(t))).sum(1)
+    P = P + V * (Gb * np.cos(delta) + Bb * np.sin(delta))
+    return SwingModel(m=m, H=H, D=D, V=V, delta=delta, G=G, B=B, P=P, Gb=Gb, Bb=Bb)
+
+
+def swing_system(model: SwingModel) -> ModalSystem:
+    """Eigen-triple of the swing model's linearisation (LAPACK through NumPy), V = U^-1."""
+    A1 = model.jacobian()
+    lam, U = np.linalg.eig(A1)
+    V = np.linalg.inv(U)
+    return ModalSystem(n=2 * model.m, A1=A1, lam=lam.astype(np.complex128),
+                       U=U.astype(np.complex128), V=V.astype(np.complex128), P=np.eye(2 * model.m))

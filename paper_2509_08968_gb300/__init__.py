@@ -75,6 +75,8 @@ def load():
     lib.npf_get_modal_slab.argtypes = [vp, ci, vp, vp]
     lib.npf_interaction.argtypes = [vp, ci, cd, vp]
     lib.npf_get_term_rows.argtypes = [vp, ci, ci, ci, vp]
+    lib.npf_set_tensor_swing.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp, vp]
+    lib.npf_get_tensor.argtypes = [vp, ci, vp]
     lib.npf_batch_compute.argtypes = [ci, vp, vp, vp]
     lib.npf_last_error.restype = ctypes.c_char_p
     lib.npf_last_status.restype = ci
@@ -166,6 +168,20 @@ class Plan:
         if not _is_torch(coeffs):
             coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
         _check(load().npf_set_tensor(self._h, order, _ptr(coeffs)))
+
+    def set_tensor_swing(self, order, model):
+        """Generate the order-`order` tensor of a swing model on the GPU (model: H, V, delta,
+        G, B, Gb, Bb as float64 arrays; n = 2 * len(H))."""
+        arrs = [np.ascontiguousarray(np.asarray(getattr(model, k), dtype=np.float64))
+                for k in ("H", "V", "delta", "G", "B", "Gb", "Bb")]
+        _check(load().npf_set_tensor_swing(self._h, order, *[_ptr(a) for a in arrs]))
+
+    def get_tensor(self, order):
+        """The plan's packed order-`order` tensor [n, C(n+order-1, order)]."""
+        from math import comb
+        out = np.empty((self.n, comb(self.n + order - 1, order)), dtype=np.float64)
+        _check(load().npf_get_tensor(self._h, order, _ptr(out)))
+        return out
 
     def compute(self, order, out=None):
         """NPF of the given order; returns a NumPy complex128 [n, n] (or fills `out`, which may

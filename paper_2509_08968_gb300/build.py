@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["npf_api.cu", "k_common.cu", "k_fp64.cu", "k_split.cu", "k_mlp.cu"]
+SOURCES = ["npf_api.cu", "k_common.cu", "k_fp64.cu", "k_split.cu", "k_mlp.cu", "k_model.cu"]
 HEADERS = ["npf_internal.h", "k_device.cuh", "k_tc.cuh"]
 
 

@@ -575,6 +575,38 @@ int npf_set_tensor(npf_handle* h, int order, const double* coeffs)
     });
 }
 
+int npf_set_tensor_swing(npf_handle* h, int order, const double* H, const double* V,
+                         const double* delta, const double* G, const double* B, const double* Gb,
+                         const double* Bb)
+{
+    return guarded([&] {
+        if (!h || !H || !V || !delta || !G || !B) npf::fail(NPF_ERR_ARG, "null argument");
+        Plan& p = h->p;
+        if (p.n % 2) npf::fail(NPF_ERR_ARG, "the swing model has 2 states per machine (n even)");
+        if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        const void* before[2] = {p.d_tensor[order], npf::split_tensor_planes(p, order)};
+        npf::swing_tensor(p, order, H, V, delta, G, B, Gb, Bb);
+        npf::split_prepare_tensor(p, order);
+        if (before[0] != p.d_tensor[order] || before[1] != npf::split_tensor_planes(p, order))
+            ++p.gen;
+        sync(p);
+    });
+}
+
+int npf_get_tensor(npf_handle* h, int order, double* out)
+{
+    return guarded([&] {
+        if (!h || !out) npf::fail(NPF_ERR_ARG, "null argument");
+        Plan& p = h->p;
+        if (order < 2 || order > p.Nmax || !p.d_tensor[order])
+            npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
+        NPF_CUDA(cudaMemcpyAsync(out, p.d_tensor[order],
+                                 (size_t)p.n * p.packed_count[order] * sizeof(double),
+                                 cudaMemcpyDefault, p.stream));
+        sync(p);
+    });
+}
+
 int npf_compute(npf_handle* h, int order, npf_c128* out)
 {
     return guarded([&] {

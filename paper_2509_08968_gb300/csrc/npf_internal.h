@@ -143,6 +143,12 @@ const void* split_tensor_planes(const Plan& p, int N);   // device address of th
 void split_refresh_modes(Plan& p);   // new modal data of the same size: re-slice in place
 
 // ----------------------------------------------------------------------------------------
+// Model tensors generated on the device (k_model.cu).
+// ----------------------------------------------------------------------------------------
+void swing_tensor(Plan& p, int N, const double* H, const double* V, const double* delta,
+                  const double* G, const double* B, const double* Gb, const double* Bb);
+
+// ----------------------------------------------------------------------------------------
 // Small shared kernels (k_common.cu).
 // ----------------------------------------------------------------------------------------
 void launch_finish(Plan& p, const double2* d_sum, double2* d_npf);   // NPF = phi o (psi + S)^T
