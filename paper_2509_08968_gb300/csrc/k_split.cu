@@ -1077,44 +1077,6 @@ __global__ void k_s_records(const double2* __restrict__ Sd, int64_t ld, int64_t 
     }
 }
 
-// Dense expansion for upper indices i in [i0, i0 + ib): row (i - i0, a_1..a_{N-1}), K pos a_N.
-template <int S>
-__global__ void k_expand(const uint4* __restrict__ rec, int64_t P, int n, int N, int i0, int ib,
-                         const int64_t* __restrict__ cnt, uint32_t* __restrict__ planes,
-                         int64_t plane_stride_u32)
-{
-    int64_t per_i = 1;
-    for (int m = 0; m < N; ++m) per_i *= NP;
-    const int64_t tot = per_i * ib;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = i0 + (int)(idx / per_i);
-        int64_t f = idx % per_i;
-        int a[8];
-        bool pad = false, unread = false;
-        for (int m = N - 1; m >= 0; --m) {
-            a[m] = (int)(f % NP);
-            f /= NP;
-            pad |= a[m] >= n;
-            if (m < N - 2) unread |= a[m] >= n;   // the contraction skips these rows' tiles
-        }
-        // rows past n in the innermost row digit only feed their own (discarded) outputs, so
-        // they are left unwritten; K' entries past n are written as zeros (they meet the fixed
-        // matrix's zero rows, where stale bit patterns could be NaN)
-        if (unread || a[N - 2] >= n) continue;
-        uint4 r0 = make_uint4(0, 0, 0, 0), r1 = make_uint4(0, 0, 0, 0);
-        if (!pad) {
-            sort_small(a, N);
-            const int64_t q = tuple_rank(a, N, cnt, n);
-            r0 = rec[((int64_t)i * P + q) * 2 + 0];
-            r1 = rec[((int64_t)i * P + q) * 2 + 1];
-        }
-        const uint32_t w[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-#pragma unroll
-        for (int s = 0; s < S; ++s) planes[s * plane_stride_u32 + idx] = w[s];
-    }
-}
-
 // Next distinct ordering of v[0..len-1] in lexicographic order (false after the last one).
 __device__ __forceinline__ bool next_ordering(int* v, int len)
 {
@@ -1132,8 +1094,9 @@ __device__ __forceinline__ bool next_ordering(int* v, int len)
 // (a_1..a_{N-1}) over [0, n)). Lane t covers a_N = lane + 32 t. The 128 K' digit records
 // S^i_{sort(prefix, a_N)} are gathered once and written to every distinct ordering of the
 // prefix (the dense rows that share them), so a record is read once per prefix rather than once
-// per ordering. Same output as k_expand (rows with an index >= n are not written; K' entries
-// past n are zeros).
+// per ordering. Layout: row (i - i0, a_1..a_{N-1}) (digits base 128), K' pair a_N; rows with an
+// index >= n are not written (they only feed their own, discarded, outputs) and K' entries past n
+// are zeros (they meet the fixed matrix's zero rows, where stale bit patterns could be NaN).
 template <int S>
 __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n, int N, int i0,
                                 int ib, const int64_t* __restrict__ cnt,

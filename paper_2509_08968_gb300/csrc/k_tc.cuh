@@ -121,15 +121,6 @@ __device__ __forceinline__ void fence_after_sync()
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 lanes x 32-bit, 8 consecutive columns per thread (lane = row of the warp's quarter).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7])
-        : "r"(taddr));
-}
 // 32 lanes x 32-bit, 4 consecutive columns per thread.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
 {
@@ -143,20 +134,10 @@ __device__ __forceinline__ void tmem_wait_ld()
 }
 
 // ---------------------------------------------------------------------------- MMA
-// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulation, one thread issues.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-// The same with the shared-memory descriptors given as 32-bit halves (low: start address and
-// leading offset, high: stride offset, version, layout) and a fixed accumulate flag, so that a
-// loop of MMAs over one stage costs a 32-bit add per operand and the instruction.
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulation, issued by one thread; the
+// shared-memory descriptors are given as 32-bit halves (low: start address and leading offset,
+// high: stride offset, version, layout) and the accumulate flag is fixed, so that a loop of MMAs
+// over one stage costs a 32-bit add per operand and the instruction.
 template <bool ACC>
 __device__ __forceinline__ void mma_bf16_lohi(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
                                               uint32_t hi, uint32_t idesc)
@@ -170,7 +151,10 @@ __device__ __forceinline__ void mma_bf16_lohi(uint32_t d_tmem, uint32_t a_lo, ui
         "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "n"(ACC ? 1 : 0)
         : "memory");
 }
-// Low and high halves of sdesc_sw64(saddr).
+// Shared-memory matrix descriptor of a K-major operand stored with the 64-byte swizzle (rows of 32
+// BF16 = 64 bytes, 8-row atoms of 512 bytes), as two 32-bit halves: start address >> 4 at bits
+// 0-13, leading byte offset (unused for swizzled K-major, 1) at 16-29; stride byte offset =
+// 512 >> 4 at bits 32-45, descriptor version 1 at 46-47, layout type SWIZZLE_64B = 4 at 61-63.
 __device__ __forceinline__ uint32_t sdesc_sw64_lo(uint32_t saddr)
 {
     return ((saddr & 0x3FFFF) >> 4) | (1u << 16);
@@ -192,21 +176,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
-}
-
-// Shared-memory matrix descriptor for a K-major operand stored with the 64-byte swizzle
-// (rows of 32 BF16 = 64 bytes, 8-row atoms of 512 bytes): start address >> 4 at bits 0-13,
-// leading byte offset (unused for swizzled K-major, 1) at 16-29, stride byte offset = 512 >> 4
-// at 32-45, descriptor version 1 at 46-47, layout type SWIZZLE_64B = 4 at bits 61-63.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
-    return d;
 }
 
 }  // namespace tc
