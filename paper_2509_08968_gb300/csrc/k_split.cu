@@ -130,8 +130,8 @@ __device__ __forceinline__ void digit_pairs(long long Wr, long long Wi, uint32_t
             fr = byte_to_digit(br, s);
             fi = byte_to_digit(bi, s);
         }
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(fr, fi);
-        out[s] = *reinterpret_cast<const uint32_t*>(&h2);
+        // both are exact BF16 values: their upper halves are the BF16 bits (Re low, Im high)
+        out[s] = __byte_perm(__float_as_uint(fr), __float_as_uint(fi), 0x7632);
     }
 }
 
@@ -228,19 +228,23 @@ struct RowInfo {
     int pad;
 };
 
-// Recombined accumulator of one output element: V (units 2^-30 of the L0 integer grid).
+// Recombined accumulator of one output element: V (units 2^-30 of the L0 integer grid). The
+// integer parts are read off float bit patterns after adding 1.5 * 2^(23 + j): the sum lands in a
+// binade whose spacing is 2^j, so it rounds to that grid (to nearest, ties to even) and its
+// mantissa bits count grid steps. L0 is an integer with |L0| <= 2^22 (256 products of digits of
+// magnitude <= 2^7); L3 * 2^30 is split into a multiple of 2^20 and an exact remainder.
 __device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t l2, uint32_t l3)
 {
-    const long long a0 = (long long)__float2int_rz(__uint_as_float(l0));
+    const int a0 = __float_as_int(__uint_as_float(l0) + 12582912.0f) - 0x4B400000;   // 1.5 * 2^23
     const long long a1 = (long long)__float2int_rn(__uint_as_float(l1) * 256.0f);
     const long long a2 = (long long)__float2int_rn(__uint_as_float(l2) * 65536.0f);
-    // rint(L3 * 2^30) with 32-bit conversions: the part above 2^20 truncated, the remainder
-    // (exact in FP32) rounded; the even multiple of 2^20 keeps the tie-to-even decision.
-    const float x3 = __uint_as_float(l3) * 1073741824.0f;
-    const int h3 = __float2int_rz(x3 * 9.5367431640625e-07f);                  // 2^-20
-    const int r3 = __float2int_rn(fmaf((float)h3, -1048576.0f, x3));            // exact remainder
+    const float x3 = __uint_as_float(l3) * 1073741824.0f;                            // 2^30
+    const float t3 = x3 + 13194139533312.0f;                                          // 1.5 * 2^43
+    const int h3 = __float_as_int(t3) - 0x55400000;          // rint(x3 / 2^20), |x3| < 2^42
+    const float r = x3 - (t3 - 13194139533312.0f);           // exact, |r| <= 2^19
+    const int r3 = __float_as_int(r + 12582912.0f) - 0x4B400000;
     const long long a3 = ((long long)h3 << 20) + r3;
-    return (a0 << 30) + (a1 << 22) + (a2 << 14) + a3;
+    return ((long long)a0 << 30) + (a1 << 22) + (a2 << 14) + a3;
 }
 
 // Upper bound of |V| 2^-30 = |L0 + L1 + L2 + L3| + (rounding of L3 to the V grid, 2^-31): the
