@@ -47,6 +47,23 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def measured_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the committed ncu
+    capture profiles/dram_<kernel>_<workload>.json, or None when there is none or when the kernel
+    sources no longer hash to the captured build's."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", f"dram_{kernel}_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    for src in d["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return d["traffic_per_launch"] if h.hexdigest() == d["sources_sha256"] else None
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) during the timed region."""
 
@@ -283,7 +300,11 @@ def main():
                 achieved = per_launch / (avg_ms * 1e-3) / 1e9
                 bound, unit, psrc = "hbm", "GB/s", f"hbm copy ({src})"
             roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
-                    "unit": unit, "frac": achieved / peak, "traffic": None, "peak_source": psrc,
+                    "unit": unit, "frac": achieved / peak,
+                    "traffic": (measured_traffic(name, args.workload)
+                                if args.precision == "split_bf16" and not (args.tile_n or args.modes)
+                                else None),
+                    "peak_source": psrc,
                     "launches": cnt, "avg_ms": avg_ms,
                     "share": tot_ms / sum(v[1] for v in prof.values())}
 
