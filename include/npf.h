@@ -152,6 +152,20 @@ int npf_get_tensor(npf_handle* h, int order, double* out);
  * Returns NPF_ERR_MISSING_TENSOR only when order >= 2 and that order's own tensor is missing. */
 int npf_compute(npf_handle* h, int order, npf_c128* out);
 
+/* npf_compute(h, order, out) while the next system's tensors upload (the tensor upload of the
+ * hot path, double-buffered): for t < count, the packed tensor of order orders[t] (2..N_max, each
+ * order at most once) at coeffs[t] (host or device; layout as npf_set_tensor) is copied on the
+ * plan's own upload stream into a staging buffer during this call's computation, which still uses
+ * the current tensors. At the start of the next call on this plan that reads tensors (compute,
+ * terms, slabs, interaction, npf_get_tensor, npf_set_tensor*, npf_batch_compute) the plan's stream
+ * waits for those copies and the staged tensors replace the current ones; the replaced buffers
+ * stage the following prefetch (one extra tensor of device memory per prefetched order). The
+ * caller keeps coeffs[t] allocated and unchanged until that next call has returned (pinned host
+ * memory lets the copy overlap; pageable memory makes it synchronous). Errors as npf_compute; a
+ * failed copy is reported by this call or the next. */
+int npf_compute_prefetch(npf_handle* h, int order, npf_c128* out, int count, const int* orders,
+                         const double* const* coeffs);
+
 /* Release every device and host resource of the plan. NULL is a no-op. */
 void npf_destroy(npf_handle* h);
 

@@ -68,6 +68,7 @@ def load():
     lib.npf_mlp_destroy.argtypes = [vp]
     lib.npf_mlp_destroy.restype = None
     lib.npf_compute.argtypes = [vp, ci, vp]
+    lib.npf_compute_prefetch.argtypes = [vp, ci, vp, ci, vp, vp]
     lib.npf_destroy.argtypes = [vp]
     lib.npf_destroy.restype = None
     lib.npf_set_option.argtypes = [vp, ci, cd]
@@ -119,6 +120,7 @@ class Plan:
     def __init__(self, lam, U, V, N_max, mem_budget=0, precision="split_bf16", stream=None):
         lib = load()
         self._keep = []
+        self._prefetched = []   # arrays whose prefetch copies the next tensor-using call waits for
         if _is_torch(lam):
             n = int(lam.shape[0])
             args = (lam, U, V)
@@ -168,6 +170,7 @@ class Plan:
         if not _is_torch(coeffs):
             coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
         _check(load().npf_set_tensor(self._h, order, _ptr(coeffs)))
+        self._prefetched = []
 
     def set_tensor_swing(self, order, model):
         """Generate the order-`order` tensor of a swing model on the GPU (model: H, V, delta,
@@ -175,12 +178,14 @@ class Plan:
         arrs = [np.ascontiguousarray(np.asarray(getattr(model, k), dtype=np.float64))
                 for k in ("H", "V", "delta", "G", "B", "Gb", "Bb")]
         _check(load().npf_set_tensor_swing(self._h, order, *[_ptr(a) for a in arrs]))
+        self._prefetched = []
 
     def get_tensor(self, order):
         """The plan's packed order-`order` tensor [n, C(n+order-1, order)]."""
         from math import comb
         out = np.empty((self.n, comb(self.n + order - 1, order)), dtype=np.float64)
         _check(load().npf_get_tensor(self._h, order, _ptr(out)))
+        self._prefetched = []
         return out
 
     def compute(self, order, out=None):
@@ -189,6 +194,26 @@ class Plan:
         if out is None:
             out = np.empty((self.n, self.n), dtype=np.complex128)
         _check(load().npf_compute(self._h, order, _ptr(out)))
+        self._prefetched = []
+        return out
+
+    def compute_prefetch(self, order, out=None, next_tensors=None):
+        """compute(order, out) while the packed tensors of `next_tensors` ({order: tensor}, host
+        or device) upload on the plan's upload stream; they replace the current tensors of those
+        orders at the next call that uses tensors, and stay referenced until that call returns."""
+        if out is None:
+            out = np.empty((self.n, self.n), dtype=np.complex128)
+        items = []
+        for N, t in (next_tensors or {}).items():
+            if not _is_torch(t):
+                t = np.ascontiguousarray(t, dtype=np.float64)
+            items.append((int(N), t))
+        orders = (ctypes.c_int * max(1, len(items)))(*[N for N, _ in items])
+        ptrs = (ctypes.c_void_p * max(1, len(items)))(*[_ptr(t).value for _, t in items])
+        pending = self._prefetched
+        self._prefetched = pending + [t for _, t in items]   # until the call has returned
+        _check(load().npf_compute_prefetch(self._h, order, _ptr(out), len(items), orders, ptrs))
+        self._prefetched = [t for _, t in items]   # the previous ones were waited for
         return out
 
     def term(self, order, out=None):
@@ -196,6 +221,7 @@ class Plan:
         if out is None:
             out = np.empty((self.n, self.n), dtype=np.complex128)
         _check(load().npf_get_term(self._h, order, _ptr(out)))
+        self._prefetched = []
         return out
 
     def interaction(self, order, delta, out=None):
@@ -204,6 +230,7 @@ class Plan:
         if out is None:
             out = np.empty((order, self.n, self.n), dtype=np.complex128)
         _check(load().npf_interaction(self._h, order, float(delta), _ptr(out)))
+        self._prefetched = []
         return out
 
     def term_rows(self, order, i_lo, i_hi, out=None):
@@ -211,6 +238,7 @@ class Plan:
         if out is None:
             out = np.empty((self.n, self.n), dtype=np.complex128)
         _check(load().npf_get_term_rows(self._h, order, int(i_lo), int(i_hi), _ptr(out)))
+        self._prefetched = []
         return out
 
     def modal_slab(self, order, prefix, out=None):
@@ -219,6 +247,7 @@ class Plan:
         if out is None:
             out = np.empty((self.n, self.n), dtype=np.complex128)
         _check(load().npf_get_modal_slab(self._h, order, _ptr(pre), _ptr(out)))
+        self._prefetched = []
         return out
 
     def profile(self, reset=False):
@@ -233,8 +262,9 @@ class Plan:
 
     def close(self):
         if getattr(self, "_h", None):
-            load().npf_destroy(self._h)
+            load().npf_destroy(self._h)   # waits for the plan's streams
             self._h = None
+        self._prefetched = []
 
     def __del__(self):
         try:
@@ -257,6 +287,8 @@ def batch_compute(plans, orders, outs):
     od = (ctypes.c_int * count)(*orders)
     op = (ctypes.c_void_p * count)(*[_ptr(o).value for o in outs])
     _check(lib.npf_batch_compute(count, hp, od, op))
+    for p in plans:
+        p._prefetched = []
     return outs
 
 

@@ -1428,6 +1428,11 @@ static void prepare_tensor(Plan& p, SplitOperand& so, int N)
     so.at_src[N] = p.d_tensor[N];
 }
 
+void split_forget_tensor(Plan& p, int N)
+{
+    if (p.split) p.split->at_src[N] = nullptr;
+}
+
 const void* split_tensor_planes(const Plan& p, int N)
 {
     return p.split ? p.split->at[N] : nullptr;

@@ -77,6 +77,42 @@ void free_plan(Plan& p)
     cudaFree(p.d_perm);
     npf::split_release(p);
     p.arena.release();
+    if (p.up_stream) {
+        cudaStreamSynchronize(p.up_stream);
+        for (int N = 0; N <= npf::kMaxOrder; ++N) {
+            cudaFree(p.d_stage[N]);
+            if (p.up_done[N]) cudaEventDestroy(p.up_done[N]);
+        }
+        cudaStreamDestroy(p.up_stream);
+    }
+}
+
+// Copy a packed order-N tensor into the plan's staging buffer on its upload stream (the tensor
+// the plan computes with stays untouched until activate_staged).
+void stage_tensor(Plan& p, int N, const double* coeffs)
+{
+    if (!p.up_stream) NPF_CUDA(cudaStreamCreateWithFlags(&p.up_stream, cudaStreamNonBlocking));
+    if (!p.up_done[N]) NPF_CUDA(cudaEventCreateWithFlags(&p.up_done[N], cudaEventDisableTiming));
+    const size_t bytes = (size_t)p.n * p.packed_count[N] * sizeof(double);
+    if (!p.d_stage[N]) NPF_CUDA(cudaMalloc(&p.d_stage[N], bytes));
+    copy_in(p.d_stage[N], coeffs, bytes, p.up_stream);
+    NPF_CUDA(cudaEventRecord(p.up_done[N], p.up_stream));
+    p.staged[N] = true;
+}
+
+// Staged tensors become the plan's tensors: the plan's stream waits for their copies, the
+// buffers swap (the replaced tensor's buffer stages the next upload), and the tensor-core forms
+// re-slice them on first use.
+void activate_staged(Plan& p)
+{
+    for (int N = 0; N <= npf::kMaxOrder; ++N) {
+        if (!p.staged[N]) continue;
+        NPF_CUDA(cudaStreamWaitEvent(p.stream, p.up_done[N], 0));
+        std::swap(p.d_tensor[N], p.d_stage[N]);
+        npf::split_forget_tensor(p, N);
+        p.staged[N] = false;
+        ++p.gen;   // recorded batch graphs address the previous buffer
+    }
 }
 
 std::atomic<uint64_t> g_next_plan_id{0};
@@ -563,6 +599,7 @@ int npf_set_tensor(npf_handle* h, int order, const double* coeffs)
         if (!h || !coeffs) npf::fail(NPF_ERR_ARG, "null handle or coeffs");
         Plan& p = h->p;
         if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        activate_staged(p);
         const size_t bytes = (size_t)p.n * p.packed_count[order] * sizeof(double);
         const void* before[2] = {p.d_tensor[order], npf::split_tensor_planes(p, order)};
         if (!p.d_tensor[order]) NPF_CUDA(cudaMalloc(&p.d_tensor[order], bytes));
@@ -584,6 +621,7 @@ int npf_set_tensor_swing(npf_handle* h, int order, const double* H, const double
         Plan& p = h->p;
         if (p.n % 2) npf::fail(NPF_ERR_ARG, "the swing model has 2 states per machine (n even)");
         if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        activate_staged(p);
         const void* before[2] = {p.d_tensor[order], npf::split_tensor_planes(p, order)};
         npf::swing_tensor(p, order, H, V, delta, G, B, Gb, Bb);
         npf::split_prepare_tensor(p, order);
@@ -598,6 +636,7 @@ int npf_get_tensor(npf_handle* h, int order, double* out)
     return guarded([&] {
         if (!h || !out) npf::fail(NPF_ERR_ARG, "null argument");
         Plan& p = h->p;
+        activate_staged(p);
         if (order < 2 || order > p.Nmax || !p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
         NPF_CUDA(cudaMemcpyAsync(out, p.d_tensor[order],
@@ -609,12 +648,31 @@ int npf_get_tensor(npf_handle* h, int order, double* out)
 
 int npf_compute(npf_handle* h, int order, npf_c128* out)
 {
+    return npf_compute_prefetch(h, order, out, 0, nullptr, nullptr);
+}
+
+int npf_compute_prefetch(npf_handle* h, int order, npf_c128* out, int count, const int* orders,
+                         const double* const* coeffs)
+{
     return guarded([&] {
         if (!h || !out) npf::fail(NPF_ERR_ARG, "null handle or out");
         Plan& p = h->p;
         if (order < 1 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [1, N_max]");
+        if (count < 0 || (count > 0 && (!orders || !coeffs)))
+            npf::fail(NPF_ERR_ARG, "bad prefetch arguments");
+        for (int t = 0; t < count; ++t) {
+            if (orders[t] < 2 || orders[t] > p.Nmax) npf::fail(NPF_ERR_ARG, "prefetch order must be in [2, N_max]");
+            if (!coeffs[t]) npf::fail(NPF_ERR_ARG, "null prefetch tensor");
+            for (int u = 0; u < t; ++u)
+                if (orders[u] == orders[t]) npf::fail(NPF_ERR_ARG, "an order appears twice in a prefetch");
+        }
+        activate_staged(p);   // tensors prefetched by the previous call
         if (order >= 2 && !p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
+        // the next tensors travel on the upload stream while this call computes on the plan's
+        // stream; the staging buffers held the tensors replaced at the last activation, whose
+        // readers finished before that call returned
+        for (int t = 0; t < count; ++t) stage_tensor(p, orders[t], coeffs[t]);
         compute_npf(p, order);
         NPF_CUDA(cudaMemcpyAsync(out, p.d_npf, (size_t)p.n * p.n * sizeof(double2),
                                  cudaMemcpyDefault, p.stream));
@@ -629,6 +687,7 @@ int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out)
         Plan& p = h->p;
         if (order < 1 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [1, N_max]");
         if (!(delta > 0.0)) npf::fail(NPF_ERR_ARG, "delta must be > 0");
+        activate_staged(p);
         const int64_t nn = (int64_t)p.n * p.n;
         // z(0) = delta Psi + sum_M delta^M Psi_M (Eq. 7; Eq. 9's corrected coordinates), kept in
         // d_sum; the per-order results go to d_npf as scratch before the copies
@@ -674,6 +733,7 @@ int npf_get_term_rows(npf_handle* h, int order, int i_lo, int i_hi, npf_c128* ou
         Plan& p = h->p;
         if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
         if (i_lo < 0 || i_hi > p.n || i_lo >= i_hi) npf::fail(NPF_ERR_ARG, "bad row range");
+        activate_staged(p);
         if (!p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
         if (p.permuted())
@@ -701,6 +761,7 @@ int npf_get_term(npf_handle* h, int order, npf_c128* out)
         if (!h || !out) npf::fail(NPF_ERR_ARG, "null handle or out");
         Plan& p = h->p;
         if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        activate_staged(p);
         if (!p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
         compute_term(p, order, p.d_psiN[order]);
@@ -721,6 +782,7 @@ int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* ou
         if (!h || !out || (!prefix && order > 1)) npf::fail(NPF_ERR_ARG, "null argument");
         Plan& p = h->p;
         if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        activate_staged(p);
         if (!p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
         if (p.permuted())
@@ -816,6 +878,7 @@ int npf_batch_compute(int count, npf_handle* const* plans, const int* orders,
             if (!plans[b] || !outs[b]) npf::fail(NPF_ERR_ARG, "null plan or output in batch");
             Plan& p = plans[b]->p;
             if (orders[b] < 1 || orders[b] > p.Nmax) npf::fail(NPF_ERR_ARG, "bad order in batch");
+            activate_staged(p);
             if (orders[b] >= 2 && !p.d_tensor[orders[b]])
                 npf::fail(NPF_ERR_MISSING_TENSOR, "missing tensor in batch");
             for (int c = 0; c < b; ++c)

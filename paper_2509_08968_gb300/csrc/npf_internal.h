@@ -117,6 +117,13 @@ struct Plan {
     Arena* shared_arena = nullptr;  // scratch shared by the plans issued on one stream
     int* err_override = nullptr;    // device error flag shared by a batch (checked by the batch)
     Arena& scratch() { return shared_arena ? *shared_arena : arena; }
+
+    // prefetched tensors (npf_compute_prefetch): copied on up_stream into d_stage while the plan
+    // computes; they replace d_tensor (buffers swapped) at the next call that uses tensors
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_done[kMaxOrder + 1] = {};
+    double* d_stage[kMaxOrder + 1] = {};
+    bool staged[kMaxOrder + 1] = {};
 };
 
 int64_t packed_count(int n, int N);
@@ -141,6 +148,7 @@ void split_release(Plan& p);
 void split_prepare_tensor(Plan& p, int N);   // digit planes of a newly uploaded tensor
 const void* split_tensor_planes(const Plan& p, int N);   // device address of those planes
 void split_refresh_modes(Plan& p);   // new modal data of the same size: re-slice in place
+void split_forget_tensor(Plan& p, int N);   // the order's tensor changed: re-slice it when used
 
 // ----------------------------------------------------------------------------------------
 // Model tensors generated on the device (k_model.cu).
