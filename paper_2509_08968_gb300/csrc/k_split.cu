@@ -279,16 +279,19 @@ __device__ __forceinline__ void load_levels(uint32_t taddr, int stride, uint32_t
     }
 }
 
-__host__ __device__ constexpr int64_t ipow_np(int e) { return e <= 0 ? 1 : NP * ipow_np(e - 1); }
+// Row digits use the radix 2^lg (32, 64 or 128 >= n): a 128-row tile holds 128 >> lg sub-blocks
+// of 2^lg rows, each one next-stage operand row (its innermost digit is the next K index).
+__host__ __device__ constexpr int64_t ipow_rad(int e, int lg) { return e <= 0 ? 1 : (int64_t)1 << (lg * e); }
 
-// digits of r (N-1 digits base NP, most significant first) into d[0..N-2]
-__device__ __forceinline__ void row_digits(int64_t r, int nd, int (&d)[8])
+// digits of r (N-1 digits base 2^lg, most significant first) into d[0..N-2]
+__device__ __forceinline__ void row_digits(int64_t r, int nd, int lg, int (&d)[8])
 {
+    const int64_t mask = ((int64_t)1 << lg) - 1;
 #pragma unroll
     for (int m = 7; m >= 0; --m) {   // unrolled with static indices: d stays in registers
         if (m < nd) {
-            d[m] = (int)(r % NP);
-            r /= NP;
+            d[m] = (int)(r & mask);
+            r >>= lg;
         } else {
             d[m] = 0;
         }
@@ -373,6 +376,7 @@ struct RowArgs {
                          // (orders <= 4 have at most two shared a's)
     int64_t R;           // rows per outer index (output layout [outer][q][r])
     int npc;             // extent of the new index in the output layout
+    int lg;              // log2 of the row radix (digits, and the next operand's K extent)
     int n;               // states (range of the a digits and of the reduction's columns k)
     int nm;              // modes in use (range of i and of the p digits; n unless a subset is set)
     int ncv;             // valid columns of this launch (modes, or states for the reduction)
@@ -417,12 +421,12 @@ struct RowCfg {
     static_assert(STAGES >= 2, "at least two pipeline stages");
 };
 
-__device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_local, int ct)
+// A sub-block (rows row0_local .. + 2^lg - 1, which share every digit but the innermost) whose
+// rows are all padding, or that the sorted-tuple rules exclude.
+__device__ __forceinline__ bool block_skipped(const RowArgs& a, int64_t row0_local, int ct)
 {
-    if (ct * a.bnc >= a.ncv) return true;                  // every column is padding
-    if (!a.digits) return false;
     int d[8];
-    row_digits(row0_local % a.R, a.N - 1, d);
+    row_digits(row0_local % a.R, a.N - 1, a.lg, d);
     const int nd = a.N - 1;
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
@@ -438,6 +442,15 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_loca
     return false;
 }
 
+__device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_local, int ct)
+{
+    if (ct * a.bnc >= a.ncv) return true;                  // every column is padding
+    if (!a.digits) return false;
+    for (int sb = 0; sb < (NP >> a.lg); ++sb)
+        if (!block_skipped(a, row0_local + ((int64_t)sb << a.lg), ct)) return false;
+    return true;
+}
+
 // First K' chunk a tile needs. In the reduction (kfrom = 1) the rows are (i, p_1..p_{N-1}) and
 // K = p_N; only non-decreasing tuples are formed, so every valid row of a tile has
 // p_N >= p_{N-1} >= p_{N-2} (its last shared digit) and the chunks below p_{N-2} are zero.
@@ -445,7 +458,7 @@ __device__ __forceinline__ int first_chunk(const RowArgs& a, int64_t row0_local)
 {
     if (!a.kfrom || a.N < 3) return 0;
     int d[8];
-    row_digits(row0_local % a.R, a.N - 1, d);
+    row_digits(row0_local % a.R, a.N - 1, a.lg, d);   // sub-block 0 has the smallest p_{N-2}
     int kmin = 0;
 #pragma unroll
     for (int m = 0; m < 8; ++m)
@@ -514,8 +527,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     uint64_t* tempty = tfull + 1;              // epilogue -> MMA: accumulators read
     uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
     int* stop = (int*)(tmem_slot + 1);
-    int* colE = (int*)(tmem_slot + 4);         // 64 column exponent keys
-    int* colEb = colE + 64;                    // 64 fixed-matrix column exponents
+    int* colE = (int*)(tmem_slot + 4);         // [4 sub-blocks][64] column exponent keys
+    int* colEb = colE + 4 * 64;                // 64 fixed-matrix column exponents
     float4* red = (float4*)(colEb + 64);       // [4 lane quarters][64 columns] reduction partials
     float2* lamf = (float2*)(red + 4 * 64);    // 64 lambda_q in FP32 (exponent estimates)
     tfl* lamt = (tfl*)(lamf + 64);             // 64 x (Re, Im) lambda_q as exact triple-floats
@@ -646,12 +659,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             const int ea = args.ea[o >> args.ea_shift];
             const int64_t outer = o / args.R;
             const int64_t rr = o % args.R;
-            const int64_t rblk = rr / NP;
-            const int64_t rperq = args.R / NP;
+            const int lg = args.lg;
+            const int64_t rblk = rr >> lg;                    // the next operand's row within [outer][q]
+            const int64_t rperq = args.R >> lg;
+            const int kpos = rl & ((1 << lg) - 1);            // ... and the K position in it
+            const int sb = rl >> lg;                          // sub-block of the tile (warp-uniform)
 
             // row digits: the first rp are p's (must be in order and < n), then a's (< n)
             int dg[8];
-            row_digits(rr, N - 1, dg);
+            row_digits(rr, N - 1, lg, dg);
             bool row_ok = true;
             int firstp = NP;
             if (args.digits) {
@@ -666,20 +682,27 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             }
 
             // rows of the swapped pair of shared a's (digits rp, rp + 1 when both are shared):
-            // offset of that row in the output's row index (shared digits, base NP)
+            // offset of that row in the output's row index (shared digits, base 2^lg). A row
+            // whose shared a's decrease is not formed: its output rows are the mirrored writes of
+            // the non-decreasing one (its operand row was never written), so it writes nothing.
             int64_t swap_off = 0;
+            bool no_write = false;
             if (MODE == EPI_SLICE && args.aswap) {
                 const int j = args.rp, nd = N - 1;
-                if (j + 1 <= nd - 2 && dg[j] < dg[j + 1]) {
-                    const int64_t wj = ipow_np(nd - 2 - j), wj1 = ipow_np(nd - 3 - j);
-                    swap_off = (int64_t)(dg[j + 1] - dg[j]) * wj + (int64_t)(dg[j] - dg[j + 1]) * wj1;
+                if (j + 1 <= nd - 2) {
+                    if (dg[j] < dg[j + 1]) {
+                        const int64_t wj = ipow_rad(nd - 2 - j, lg), wj1 = ipow_rad(nd - 3 - j, lg);
+                        swap_off = (int64_t)(dg[j + 1] - dg[j]) * wj + (int64_t)(dg[j] - dg[j + 1]) * wj1;
+                    }
+                    no_write = dg[j] > dg[j + 1];
                 }
             }
             // per-tile tables: column exponents, the fixed matrix's column exponents, lambda_q
             // (FP32 and as exact triple-floats); per row (one thread of each row): sigma of the
             // row p's minus lambda_i, the multiplicity base and the first run length
             if (et < 64) {
-                colE[et] = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) colE[64 * b + et] = 0;
                 colEb[et] = args.eb[qbase + et];
                 if (MODE == EPI_DIVIDE) {
                     const int q = qbase + et;
@@ -786,7 +809,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             // L3) 2^30): the FP32 sum plus its worst rounding error
                             const float br = level_bound(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                             const float bi = level_bound(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                            const bool valid = row_ok && qc < args.ncv && (!args.colmask || qc <= firstp);
+                            const bool valid = row_ok && !no_write && qc < args.ncv &&
+                                               (!args.colmask || qc <= firstp);
                             unsigned key = 0;
                             if (MODE == EPI_SLICE) {
                                 // bitlen(V) <= exponent(bound) + 30
@@ -808,7 +832,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                                 key = (unsigned)(f32_exponent(hm) + 30 + ea + eb - VEXP + 8192);
                             }
                             const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
-                            if (lane == 0 && wmax) atomicMax(&colE[cl], (int)wmax);
+                            if (lane == 0 && wmax) atomicMax(&colE[64 * sb + cl], (int)wmax);
                         }
                     }
                 }
@@ -933,8 +957,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             continue;
                         }
                         if (args.colmask && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
+                        if (no_write) continue;
                         const int64_t rowp = (outer * args.npc + qc) * rperq + rblk;
-                        const int key = colE[cl];
+                        const int key = colE[64 * sb + cl];
                         const int E = key ? key - 8192 : EXP_NONE;
                         uint32_t w[S];
                         if (key == 0 || !valid) {
@@ -975,15 +1000,16 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             digit_pairs<S>(df_round_i64(dfl{ldexpf(qr.hi, k), ldexpf(qr.lo, k)}),
                                            df_round_i64(dfl{ldexpf(qi.hi, k), ldexpf(qi.lo, k)}), w);
                         }
-                        uint32_t* dst = reinterpret_cast<uint32_t*>(args.out_planes) + rowp * (KP / 2) + rl;
+                        // next operand row rowp: 2^lg complex K entries (BF16 pairs), K = kpos
+                        uint32_t* dst = reinterpret_cast<uint32_t*>(args.out_planes) + (rowp << lg) + kpos;
 #pragma unroll
                         for (int s = 0; s < S; ++s) dst[s * (args.out_plane_stride / 2)] = w[s];
-                        if (rl == 0) args.out_exp[rowp] = E;
+                        if (kpos == 0) args.out_exp[rowp] = E;
                         if (MODE == EPI_SLICE && swap_off != 0) {   // the same row, shared a's swapped
-                            uint32_t* d2 = dst + swap_off * (KP / 2);
+                            uint32_t* d2 = dst + (swap_off << lg);
 #pragma unroll
                             for (int s = 0; s < S; ++s) d2[s * (args.out_plane_stride / 2)] = w[s];
-                            if (rl == 0) args.out_exp[rowp + swap_off] = E;
+                            if (kpos == 0) args.out_exp[rowp + swap_off] = E;
                         }
                     }
                 }
@@ -995,21 +1021,25 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const int cl = et;
                 const int qc = qbase + cl;
                 if (ok && cl < bnc && qc < args.ncv) {
-                    dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
-                    for (int pp = 0; pp < 4; ++pp) {
-                        const float4 g = red[pp * 64 + cl];
-                        ar = df_add(ar, dfl{g.x, g.y});
-                        ai = df_add(ai, dfl{g.z, g.w});
-                    }
-                    if (ar.hi != 0.f || ai.hi != 0.f) {
-                        // the tile shares (i, p_1..p_{N-2}): recover them from its first row
+                    // each sub-block shares (i, p_1..p_{N-2}); its lane quarters' partials
+                    const int nsb = NP >> args.lg, qps = 4 / nsb;
+                    for (int b = 0; b < nsb; ++b) {
+                        dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
+                        for (int pp = 0; pp < qps; ++pp) {
+                            const float4 g = red[(b * qps + pp) * 64 + cl];
+                            ar = df_add(ar, dfl{g.x, g.y});
+                            ai = df_add(ai, dfl{g.z, g.w});
+                        }
+                        if (ar.hi == 0.f && ai.hi == 0.f) continue;
+                        // recover (i, p_1..p_{N-2}) from the sub-block's first row
+                        const int64_t rb = row0 + ((int64_t)b << args.lg);
                         int d0[8];
-                        row_digits((row0 % args.R), N - 1, d0);
+                        row_digits(rb % args.R, N - 1, args.lg, d0);
                         double2 wgt = make_double2(1.0, 0.0);
 #pragma unroll
                         for (int m = 0; m < 6; ++m)
                             if (m < N - 2) wgt = cmul(wgt, args.V[(int64_t)d0[m] * n + qc]);
-                        const int i = args.i0 + (int)(row0 / args.R);
+                        const int i = args.i0 + (int)(rb / args.R);
                         const double2 v = cmul(make_double2(df_to_d(ar), df_to_d(ai)), wgt);
                         atomicAdd(&args.out_f64[(int64_t)i * n + qc].x, -v.x);
                         atomicAdd(&args.out_f64[(int64_t)i * n + qc].y, -v.y);
@@ -1098,12 +1128,13 @@ __device__ __forceinline__ bool next_ordering(int* v, int len)
 // (a_1..a_{N-1}) over [0, n)). Lane t covers a_N = lane + 32 t. The 128 K' digit records
 // S^i_{sort(prefix, a_N)} are gathered once and written to every distinct ordering of the
 // prefix (the dense rows that share them), so a record is read once per prefix rather than once
-// per ordering. Layout: row (i - i0, a_1..a_{N-1}) (digits base 128), K' pair a_N; rows with an
-// index >= n are not written (they only feed their own, discarded, outputs) and K' entries past n
-// are zeros (they meet the fixed matrix's zero rows, where stale bit patterns could be NaN).
+// per ordering. Layout: row (i - i0, a_1..a_{N-1}) (digits base 2^lg >= n), K' pair a_N (2^lg
+// pairs a row); rows with an index >= n are not written (they only feed their own, discarded,
+// outputs) and K' entries past n are zeros (they meet the fixed matrix's zero rows, where stale
+// bit patterns could be NaN).
 template <int S>
 __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n, int N, int i0,
-                                int ib, const int64_t* __restrict__ cnt,
+                                int ib, int lg, const int64_t* __restrict__ cnt,
                                 const uint32_t* __restrict__ prefixes, int64_t npre,
                                 uint32_t* __restrict__ planes, int64_t plane_stride_u32)
 {
@@ -1111,8 +1142,8 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nd = N - 1;
-    int64_t rows_per_i = 1;
-    for (int m = 0; m < nd; ++m) rows_per_i *= NP;
+    const int64_t rows_per_i = ipow_rad(nd, lg);
+    const int kw = 1 << lg;   // K' pairs a row
     for (int64_t item = warp; item < npre * ib; item += nwarps) {
         const int il = (int)(item / npre);
         const uint32_t pk = prefixes[item % npre];
@@ -1149,12 +1180,13 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
             for (int m = 1; m < nd - 1; ++m) sorted_shared &= ord[m - 1] <= ord[m];
             if (!sorted_shared) continue;
             int64_t row = 0;
-            for (int m = 0; m < nd; ++m) row = row * NP + ord[m];
-            uint32_t* dst = planes + ((int64_t)il * rows_per_i + row) * NP + lane;
+            for (int m = 0; m < nd; ++m) row = (row << lg) + ord[m];
+            uint32_t* dst = planes + (((int64_t)il * rows_per_i + row) << lg) + lane;
 #pragma unroll
             for (int t = 0; t < 4; ++t)
+                if (32 * t < kw)
 #pragma unroll
-                for (int s = 0; s < S; ++s) dst[s * plane_stride_u32 + 32 * t] = w[t][s];
+                    for (int s = 0; s < S; ++s) dst[s * plane_stride_u32 + 32 * t] = w[t][s];
         } while (next_ordering(ord, nd));
     }
 }
@@ -1554,19 +1586,25 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const int nm = p.nm;                 // modes in use (a critical-mode subset comes first)
     const int64_t P = p.packed_count[N];
     const int64_t Prows = so.at_rows[N];
-    const int64_t npN1 = ipow64(NP, N - 1);
+    // row radix 2^lg >= n: 32 or 64 for small systems of order >= 3 (a 128-row tile then holds
+    // 4 or 2 operand rows instead of one padded to 128), else 128; with N >= 3 a tile never
+    // straddles two upper indices (2^(lg (N-1)) is a multiple of 128)
+    const int lg = (N >= 3 && n <= 32) ? 5 : (N >= 3 && n <= 64) ? 6 : 7;
+    const int rad = 1 << lg;
+    const int64_t npN1 = ipow64(rad, N - 1);
+    const int bnc = std::min(p.tile_n, rad);
     const bool slab = prefix != nullptr;
 
     // ---- memory plan (Algorithm 1's rule on the upper-index space)
     const size_t s_bytes = (size_t)n * Prows * sizeof(double2);
     const size_t rec_bytes = (size_t)n * P * 32;
-    const size_t per_i = 2 * ((size_t)npN1 * KP * 2 * S + (size_t)npN1 * 4) + 4096;
+    const size_t per_i = 2 * ((size_t)npN1 * 2 * rad * 2 * S + (size_t)npN1 * 4) + 4096;
     const size_t budget = effective_budget(p);
     if (s_bytes + rec_bytes + per_i > budget)
         fail(NPF_ERR_OOM, "memory budget too small for one upper-index batch");
     const int ib = (int)std::min<size_t>((size_t)nm, (budget - s_bytes - rec_bytes) / per_i);
     const int64_t t_rows = (int64_t)ib * npN1;
-    const size_t tbytes = (size_t)t_rows * KP * 2 * S;
+    const size_t tbytes = (size_t)t_rows * 2 * rad * 2 * S;
     const size_t ebytes = (size_t)t_rows * 4;
     Arena& ar = p.scratch();
     ar.reserve(s_bytes + rec_bytes + 2 * (tbytes + ebytes) + 8 * 256 + 1024);
@@ -1580,12 +1618,12 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
 
     if (!slab) launch_zero(p, d_out, (int64_t)n * n);
 
-    const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, p.tile_n);
-    const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, p.tile_n);
-    const CUtensorMap tRed = make_tmap(W ? so.wred : so.red, KP, (int64_t)S * 512, p.tile_n);
+    const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, bnc);
+    const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, bnc);
+    const CUtensorMap tRed = make_tmap(W ? so.wred : so.red, KP, (int64_t)S * 512, bnc);
     const CUtensorMap tAT = make_tmap(so.at[N], NP, (int64_t)S * Prows, 128);
-    const CUtensorMap tT0 = make_tmap(T[0], KP, (int64_t)S * t_rows, 128);
-    const CUtensorMap tT1 = make_tmap(T[1], KP, (int64_t)S * t_rows, 128);
+    const CUtensorMap tT0 = make_tmap(T[0], 2 * rad, (int64_t)S * t_rows, 128);
+    const CUtensorMap tT1 = make_tmap(T[1], 2 * rad, (int64_t)S * t_rows, 128);
     const CUtensorMap* tT[2] = {&tT0, &tT1};
 
     RowArgs base0{};
@@ -1603,8 +1641,9 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     base0.stall = p.debug_stall;
     base0.eps2f = (float)(p.eps * p.eps);
     base0.err = err;
-    base0.bnc = p.tile_n;
-    base0.ncol_tiles = NP / p.tile_n;
+    base0.bnc = bnc;
+    base0.ncol_tiles = rad / bnc;
+    base0.lg = lg;
     if (slab)
         for (int m = 0; m < N - 1; ++m) base0.pre[m] = prefix[m];
 
@@ -1619,6 +1658,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         a.eb = so.psir_e;
         a.num_tiles = Prows / NP * a.ncol_tiles;
         a.digits = 0;
+        a.lg = 7;                    // plain rows (packed tuples), no digits
         a.R = Prows;
         a.npc = n;
         a.out_f64 = Sd;
@@ -1639,9 +1679,9 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         const int64_t rows = (int64_t)cur * npN1;
         {
             LaunchScope ls(&p.prof, "split_expand", p.stream);
-            k_expand_sorted<S><<<8192, 256, 0, p.stream>>>(rec, P, n, N, i0, cur, p.d_cnt,
+            k_expand_sorted<S><<<8192, 256, 0, p.stream>>>(rec, P, n, N, i0, cur, lg, p.d_cnt,
                                                            so.prefixes[N], so.nprefix[N],
-                                                           (uint32_t*)T[0], t_rows * (KP / 2));
+                                                           (uint32_t*)T[0], t_rows * rad);
             NPF_CUDA(cudaGetLastError());
         }
         int cb = 0;
@@ -1651,7 +1691,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
             a.kch = (2 * n + BK - 1) / BK;   // K' = 2 p + re/im < 2 n
             a.klast = (2 * n + 15) / 16 - 2 * (a.kch - 1);
             a.ea = c == 1 ? sE + i0 : E[cb];
-            a.ea_shift = c == 1 ? 7 * (N - 1) : 0;
+            a.ea_shift = c == 1 ? lg * (N - 1) : 0;   // c = 1: one exponent per upper index
             a.eb = so.phi_e;
             a.num_tiles = rows / NP * a.ncol_tiles;
             a.digits = 1;
@@ -1659,10 +1699,10 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
             a.colmask = c >= 2;        // new index p_{N-c+1} <= p_{N-c+2}
             a.aswap = c < N;           // mode products: shared a's non-decreasing, rows mirrored
             a.R = npN1;
-            a.npc = NP;
+            a.npc = rad;
             a.i0 = i0;
             a.out_planes = T[cb ^ 1];
-            a.out_plane_stride = t_rows * KP;
+            a.out_plane_stride = t_rows * 2 * rad;
             a.out_exp = E[cb ^ 1];
             if (c < N) {
                 launch_rows<S, EPI_SLICE>(p, "split_mode_product", *tT[cb], tPhi, a);
@@ -1690,7 +1730,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         a.rp = N - 1;
         a.colmask = 0;
         a.R = npN1;
-        a.npc = NP;
+        a.npc = rad;
         a.i0 = i0;
         a.out_f64 = d_out;
         launch_rows<S, EPI_REDUCE>(p, "split_reduce", *tT[cb], tRed, a);
