@@ -423,10 +423,10 @@ struct RowCfg {
 
 // A sub-block (rows row0_local .. + 2^lg - 1, which share every digit but the innermost) whose
 // rows are all padding, or that the sorted-tuple rules exclude.
-__device__ __forceinline__ bool block_skipped(const RowArgs& a, int64_t row0_local, int ct)
+__device__ __forceinline__ bool block_skipped(const RowArgs& a, int lg, int64_t row0_local, int ct)
 {
     int d[8];
-    row_digits(row0_local % a.R, a.N - 1, a.lg, d);
+    row_digits(row0_local % a.R, a.N - 1, lg, d);
     const int nd = a.N - 1;
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
@@ -442,23 +442,24 @@ __device__ __forceinline__ bool block_skipped(const RowArgs& a, int64_t row0_loc
     return false;
 }
 
-__device__ __forceinline__ bool tile_skipped(const RowArgs& a, int64_t row0_local, int ct)
+// lg: the row radix (a compile-time 7 in the kernels without sub-blocks)
+__device__ __forceinline__ bool tile_skipped(const RowArgs& a, int lg, int64_t row0_local, int ct)
 {
     if (ct * a.bnc >= a.ncv) return true;                  // every column is padding
     if (!a.digits) return false;
-    for (int sb = 0; sb < (NP >> a.lg); ++sb)
-        if (!block_skipped(a, row0_local + ((int64_t)sb << a.lg), ct)) return false;
+    for (int sb = 0; sb < (NP >> lg); ++sb)
+        if (!block_skipped(a, lg, row0_local + ((int64_t)sb << lg), ct)) return false;
     return true;
 }
 
 // First K' chunk a tile needs. In the reduction (kfrom = 1) the rows are (i, p_1..p_{N-1}) and
 // K = p_N; only non-decreasing tuples are formed, so every valid row of a tile has
 // p_N >= p_{N-1} >= p_{N-2} (its last shared digit) and the chunks below p_{N-2} are zero.
-__device__ __forceinline__ int first_chunk(const RowArgs& a, int64_t row0_local)
+__device__ __forceinline__ int first_chunk(const RowArgs& a, int lg, int64_t row0_local)
 {
     if (!a.kfrom || a.N < 3) return 0;
     int d[8];
-    row_digits(row0_local % a.R, a.N - 1, a.lg, d);   // sub-block 0 has the smallest p_{N-2}
+    row_digits(row0_local % a.R, a.N - 1, lg, d);   // sub-block 0 has the smallest p_{N-2}
     int kmin = 0;
 #pragma unroll
     for (int m = 0; m < 8; ++m)
@@ -512,7 +513,7 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r
 //   warps 2..9       : epilogue (lane quarter = warp % 4, column half = (warp - 2) / 4). Values
 //                      needed twice (a column exponent before slicing) are read from TMEM twice
 //                      instead of being staged in shared memory.
-template <int S, int MODE>
+template <int S, int MODE, bool SUBB>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
     k_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            RowArgs args)
@@ -540,6 +541,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     const uint32_t b_bytes_tile = (uint32_t)bnr * BK * 2;
     const int64_t ntiles = args.num_tiles;
     const int ncol = args.ncol_tiles;
+    const int lg = SUBB ? args.lg : 7;         // row radix 2^lg (sub-blocks only below 128)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -569,9 +571,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
                 const int ct = (int)(tile % ncol);
                 const int64_t row0 = tile / ncol * NP;
-                if (tile_skipped(args, row0, ct)) continue;
+                if (tile_skipped(args, lg, row0, ct)) continue;
                 const int bc = ct * bnc;
-                for (int kc = first_chunk(args, row0); kc < args.kch; ++kc, ++it) {
+                for (int kc = first_chunk(args, lg, row0); kc < args.kch; ++kc, ++it) {
                     const int st = (int)(it % C::STAGES);
                     const uint32_t ph = (it / C::STAGES) & 1;
                     if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) {
@@ -608,10 +610,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
                 const int ct = (int)(tile % ncol);
                 const int64_t row0 = tile / ncol * NP;
-                if (tile_skipped(args, row0, ct)) continue;
+                if (tile_skipped(args, lg, row0, ct)) continue;
                 if (!tc::mbar_wait(tempty, (t & 1) ^ 1, args.err, kErrTimeout)) break;
                 tc::fence_after_sync();
-                const int kc0 = first_chunk(args, row0);
+                const int kc0 = first_chunk(args, lg, row0);
                 for (int kc = kc0; kc < args.kch; ++kc, ++it) {
                     const int st = (int)(it % C::STAGES);
                     const uint32_t ph = (it / C::STAGES) & 1;
@@ -652,14 +654,13 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const int ct = (int)(tile % ncol);
             const int64_t row0 = tile / ncol * NP;
-            if (tile_skipped(args, row0, ct)) continue;
+            if (tile_skipped(args, lg, row0, ct)) continue;
             unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
             const int qbase = ct * bnc;
             const int64_t o = row0 + rl;                      // local row of the launch
             const int ea = args.ea[o >> args.ea_shift];
             const int64_t outer = o / args.R;
             const int64_t rr = o % args.R;
-            const int lg = args.lg;
             const int64_t rblk = rr >> lg;                    // the next operand's row within [outer][q]
             const int64_t rperq = args.R >> lg;
             const int kpos = rl & ((1 << lg) - 1);            // ... and the K position in it
@@ -694,7 +695,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         const int64_t wj = ipow_rad(nd - 2 - j, lg), wj1 = ipow_rad(nd - 3 - j, lg);
                         swap_off = (int64_t)(dg[j + 1] - dg[j]) * wj + (int64_t)(dg[j] - dg[j + 1]) * wj1;
                     }
-                    no_write = dg[j] > dg[j + 1];
+                    no_write = SUBB && dg[j] > dg[j + 1];   // (whole tiles are skipped at radix 128)
                 }
             }
             // per-tile tables: column exponents, the fixed matrix's column exponents, lambda_q
@@ -1022,7 +1023,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const int qc = qbase + cl;
                 if (ok && cl < bnc && qc < args.ncv) {
                     // each sub-block shares (i, p_1..p_{N-2}); its lane quarters' partials
-                    const int nsb = NP >> args.lg, qps = 4 / nsb;
+                    const int nsb = NP >> lg, qps = 4 / nsb;
                     for (int b = 0; b < nsb; ++b) {
                         dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
                         for (int pp = 0; pp < qps; ++pp) {
@@ -1032,9 +1033,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         }
                         if (ar.hi == 0.f && ai.hi == 0.f) continue;
                         // recover (i, p_1..p_{N-2}) from the sub-block's first row
-                        const int64_t rb = row0 + ((int64_t)b << args.lg);
+                        const int64_t rb = row0 + ((int64_t)b << lg);
                         int d0[8];
-                        row_digits(rb % args.R, N - 1, args.lg, d0);
+                        row_digits(rb % args.R, N - 1, lg, d0);
                         double2 wgt = make_double2(1.0, 0.0);
 #pragma unroll
                         for (int m = 0; m < 6; ++m)
@@ -1340,16 +1341,27 @@ void split_release(Plan& p)
     p.split = nullptr;
 }
 
+template <int S, int MODE, bool SUBB>
+static void smem_attr()
+{
+    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, MODE, SUBB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  RowCfg<S>::SMEM));
+}
+
 template <int S>
 static void set_smem_attrs()
 {
     static bool done = false;
     if (done) return;
-    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_F64T>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_SLICE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_DIVIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_SLAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
-    NPF_CUDA(cudaFuncSetAttribute(k_rows<S, EPI_REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<S>::SMEM));
+    smem_attr<S, EPI_F64T, false>();   // packed-tuple rows: never sub-blocks
+    smem_attr<S, EPI_SLICE, false>();
+    smem_attr<S, EPI_SLICE, true>();
+    smem_attr<S, EPI_DIVIDE, false>();
+    smem_attr<S, EPI_DIVIDE, true>();
+    smem_attr<S, EPI_SLAB, false>();
+    smem_attr<S, EPI_SLAB, true>();
+    smem_attr<S, EPI_REDUCE, false>();
+    smem_attr<S, EPI_REDUCE, true>();
     done = true;
 }
 
@@ -1541,7 +1553,13 @@ static void launch_rows(Plan& p, const char* name, const CUtensorMap& tA, const 
         // row tile differ in cost under the sorted-tuple masks)
         int64_t grid = std::min<int64_t>(a.num_tiles, sm_count());
         if (grid > 1 && a.ncol_tiles > 1 && grid % 2 == 0) grid -= 1;
-        k_rows<S, MODE><<<(unsigned)std::max<int64_t>(grid, 1), ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+        const unsigned g = (unsigned)std::max<int64_t>(grid, 1);
+        if constexpr (MODE != EPI_F64T) {
+            if (a.lg < 7) k_rows<S, MODE, true><<<g, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+            else k_rows<S, MODE, false><<<g, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+        } else {
+            k_rows<S, MODE, false><<<g, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+        }
         NPF_CUDA(cudaGetLastError());
     }
     if (tracing) {
