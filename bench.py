@@ -436,9 +436,9 @@ def run_batch(args, world, rank, local, dist):
         f *= pairs
         t = args.tile_n or npf.tuned_tile(n, N, args.precision) or 64
         tiles[f"n{n}o{N}"] = t
-        # padded tile shape: the row radix (32 / 64 / 128 >= n for orders >= 3, else 128) per
-        # innermost row index, K' in chunks of 32, t columns
-        rad = 32 if (N >= 3 and n <= 32) else 64 if (N >= 3 and n <= 64) else 128
+        # padded tile shape: the row radix (32 / 64 / 128 >= n) per innermost row index, K' in
+        # chunks of 32, t columns
+        rad = 32 if n <= 32 else 64 if n <= 64 else 128
         r = (rad / n) * (32 * -(-2 * n // 32) / (2 * n)) * (t * -(-n // t) / n)
         useful += f
         executed += f * r

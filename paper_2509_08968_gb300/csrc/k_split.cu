@@ -348,11 +348,12 @@ __global__ void k_prep_at(const double* __restrict__ A, int64_t P, int n,
 // Row-data GEMM: data rows on the M side (128 per tile), the fixed complex matrix on the N side
 // (bnc complex columns per tile -> 2*bnc real columns: Re block then Im block).
 //
-// A launch works on rows o = outer * R + r where r holds N-1 base-128 digits (most significant
-// first): `rp` leading lower output indices p followed by lower input indices a; the innermost
-// digit varies within a 128-row tile, the others are shared by the tile. The non-decreasing rule
-// (only p's in order, new column <= first p when `colmask`) and the padding (digits >= n) decide
-// which tiles run and which elements count.
+// A launch works on rows o = outer * R + r where r holds N-1 base-2^lg digits (most significant
+// first; 2^lg = 32, 64 or 128 >= n): `rp` leading lower output indices p followed by lower input
+// indices a. The innermost digit varies within a sub-block of 2^lg rows, the others are shared by
+// it; a 128-row tile holds 128 >> lg sub-blocks. The non-decreasing rule (only p's in order, new
+// column <= first p when `colmask`) and the padding (digits >= n) decide which tiles run (a tile
+// runs when any sub-block does) and which elements count.
 // ---------------------------------------------------------------------------------------
 enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3, EPI_REDUCE = 4 };
 
@@ -380,6 +381,7 @@ struct RowArgs {
     int n;               // states (range of the a digits and of the reduction's columns k)
     int nm;              // modes in use (range of i and of the p digits; n unless a subset is set)
     int ncv;             // valid columns of this launch (modes, or states for the reduction)
+    int nouter;          // upper indices of this launch: rows of later ones pad the last tile
     __nv_bfloat16* out_planes;
     int64_t out_plane_stride;
     int* out_exp;
@@ -680,6 +682,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     }
                 }
                 if (args.rp >= 1) firstp = dg[0];
+                if (SUBB) row_ok &= outer < args.nouter;
             }
 
             // rows of the swapped pair of shared a's (digits rp, rp + 1 when both are shared):
@@ -698,6 +701,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     no_write = SUBB && dg[j] > dg[j + 1];   // (whole tiles are skipped at radix 128)
                 }
             }
+            if (SUBB && outer >= args.nouter) no_write = true;   // padding rows past the batch
             // per-tile tables: column exponents, the fixed matrix's column exponents, lambda_q
             // (FP32 and as exact triple-floats); per row (one thread of each row): sigma of the
             // row p's minus lambda_i, the multiplicity base and the first run length
@@ -1604,10 +1608,10 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const int nm = p.nm;                 // modes in use (a critical-mode subset comes first)
     const int64_t P = p.packed_count[N];
     const int64_t Prows = so.at_rows[N];
-    // row radix 2^lg >= n: 32 or 64 for small systems of order >= 3 (a 128-row tile then holds
-    // 4 or 2 operand rows instead of one padded to 128), else 128; with N >= 3 a tile never
-    // straddles two upper indices (2^(lg (N-1)) is a multiple of 128)
-    const int lg = (N >= 3 && n <= 32) ? 5 : (N >= 3 && n <= 64) ? 6 : 7;
+    // row radix 2^lg >= n: 32 or 64 for small systems (a 128-row tile then holds 4 or 2 operand
+    // rows instead of one padded to 128), else 128. For order 2 a tile can span several upper
+    // indices, and the rows of a batch are padded to whole tiles (rows past it write nothing).
+    const int lg = n <= 32 ? 5 : n <= 64 ? 6 : 7;
     const int rad = 1 << lg;
     const int64_t npN1 = ipow64(rad, N - 1);
     const int bnc = std::min(p.tile_n, rad);
@@ -1621,7 +1625,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     if (s_bytes + rec_bytes + per_i > budget)
         fail(NPF_ERR_OOM, "memory budget too small for one upper-index batch");
     const int ib = (int)std::min<size_t>((size_t)nm, (budget - s_bytes - rec_bytes) / per_i);
-    const int64_t t_rows = (int64_t)ib * npN1;
+    const int64_t t_rows = ((int64_t)ib * npN1 + NP - 1) / NP * NP;
     const size_t tbytes = (size_t)t_rows * 2 * rad * 2 * S;
     const size_t ebytes = (size_t)t_rows * 4;
     Arena& ar = p.scratch();
@@ -1694,7 +1698,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const int rhi = p.row_hi < 0 ? nm : std::min(p.row_hi, nm);
     for (int i0 = rlo; i0 < rhi; i0 += ib) {
         const int cur = std::min(ib, rhi - i0);
-        const int64_t rows = (int64_t)cur * npN1;
+        const int64_t rows = ((int64_t)cur * npN1 + NP - 1) / NP * NP;   // whole tiles
         {
             LaunchScope ls(&p.prof, "split_expand", p.stream);
             k_expand_sorted<S><<<8192, 256, 0, p.stream>>>(rec, P, n, N, i0, cur, lg, p.d_cnt,
@@ -1719,6 +1723,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
             a.R = npN1;
             a.npc = rad;
             a.i0 = i0;
+            a.nouter = cur;
             a.out_planes = T[cb ^ 1];
             a.out_plane_stride = t_rows * 2 * rad;
             a.out_exp = E[cb ^ 1];
@@ -1750,6 +1755,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         a.R = npN1;
         a.npc = rad;
         a.i0 = i0;
+        a.nouter = cur;
         a.out_f64 = d_out;
         launch_rows<S, EPI_REDUCE>(p, "split_reduce", *tT[cb], tRed, a);
     }
