@@ -195,6 +195,9 @@ def main():
                     help="complex columns per tensor-core tile (16/32/64; 0 = library default)")
     ap.add_argument("--modes", type=int, default=0,
                     help="critical-mode subset: the m least-damped modes (0 = all modes)")
+    ap.add_argument("--mem-budget", type=float, default=0.0,
+                    help="device memory for intermediates in GB (0 = the library default, 80%% of "
+                         "free memory); small values keep profiler captures small")
     ap.add_argument("--workload", default="n120", choices=list(WORKLOADS),
                     help="n120: the measured configuration; the others are small cases for "
                          "profiler captures")
@@ -233,6 +236,8 @@ def main():
                     stream=stream.cuda_stream)
     if args.tile_n:
         plan.set_option(npf.OPT_TILE_N, args.tile_n)
+    if args.mem_budget:
+        plan.set_option(npf.OPT_MEM_BUDGET, args.mem_budget * 2**30)
     subset = None
     if args.modes and args.modes < n:
         # least damped first (largest real part), ties by index
