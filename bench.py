@@ -135,6 +135,19 @@ def dist_setup():
     return world, rank, local
 
 
+def workload_config(n, orders, precision, swing=False, modes=None):
+    """The `config` of a single-system workload line (both arms)."""
+    return {"workload": (f"n={n} swing model ({n // 2} machines, ring + random lines), NPF orders "
+                         f"{', '.join(map(str, orders))}, derivative tensors generated on the GPU")
+                        if swing else
+                        (f"n={n} block-structured system ({n // 4} blocks x 4 states), NPF orders "
+                         f"{', '.join(map(str, orders))}, packed symmetric tensors 30% N(0,1)"),
+            "n": n, "orders": list(orders), "precision": precision,
+            "entries_per_step": sum((modes or n) ** (N + 1) for N in orders),
+            "modes": modes or n,
+            "l2": "inputs larger than L2 (packed order-4 tensor 8.7 GB)"}
+
+
 def cpu_baseline(seconds_budget=20.0):
     """The CPU oracle as it stands on the host cores: order-3 modal contraction plus reduction
     of the n = 120 system for as many leading p_1 values as fit the time budget."""
@@ -157,24 +170,32 @@ def cpu_baseline(seconds_budget=20.0):
 
 
 def run_reference(args):
+    """The CPU oracle on the default workload's config: every step is a bounded sample of it (the
+    order-3 contraction and reduction for the leading p_1 values that fit the step's budget), the
+    value its entries per second."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
+    budget = min(20.0, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        pass
-    vals = []
+        cpu_baseline(seconds_budget=min(budget, 2.0))
+    vals, secs = [], []
     cb = None
     for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(seconds_budget=min(20.0, 150.0 / max(1, args.steps)))
+        t0 = time.perf_counter()
+        cb = cpu_baseline(seconds_budget=budget)
+        secs.append(time.perf_counter() - t0)
         vals.append(cb["value"])
     v = statistics.median(vals)
     cb["value"] = v
+    cb["sample_ms_per_step"] = statistics.median(secs) * 1e3
+    config = workload_config(N_STATES, ORDERS, "fp64 (CPU oracle)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "entries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "n=120 block-structured system, order 3 sample (CPU oracle)",
-                       "n": N_STATES, "orders": [3]},
+            # a whole step of the workload at the sampled rate (each timed step is a sample)
+            "ms_per_step": config["entries_per_step"] / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "entries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -363,15 +384,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision],
             "data": "synthetic",
-            "config": {"workload": (f"n={n} swing model ({n // 2} machines, ring + random lines), "
-                                    f"NPF orders {', '.join(map(str, ORDERS))}, derivative tensors "
-                                    "generated on the GPU") if swing else
-                                   (f"n={n} block-structured system ({n // 4} blocks x 4 states), "
-                                    f"NPF orders {', '.join(map(str, ORDERS))}, packed symmetric "
-                                    "tensors 30% N(0,1)"),
-                       "n": n, "orders": list(ORDERS), "precision": args.precision,
-                       "entries_per_step": ents_rank, "modes": m_modes,
-                       "l2": "inputs larger than L2 (packed order-4 tensor 8.7 GB)"},
+            "config": workload_config(n, ORDERS, args.precision, swing, m_modes),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         }
