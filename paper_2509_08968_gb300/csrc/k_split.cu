@@ -1614,7 +1614,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const int lg = n <= 32 ? 5 : n <= 64 ? 6 : 7;
     const int rad = 1 << lg;
     const int64_t npN1 = ipow64(rad, N - 1);
-    const int bnc = std::min(p.tile_n, rad);
+    // complex columns per tile (the slab path runs untuned: 64 when the plan autotunes)
+    const int bnc = std::min(p.tile_n > 0 ? p.tile_n : 64, rad);
     const bool slab = prefix != nullptr;
 
     // ---- memory plan (Algorithm 1's rule on the upper-index space)

@@ -53,3 +53,38 @@ def test_radix_multi_batch(npf, n, N):
         small = p.term(N)
     assert rel_fro(full, ref) < 1e-10
     assert rel_fro(small, ref) < 1e-10
+
+
+def test_autotuned_plan_term_and_slab(npf):
+    """Tile width left to the autotuner (0): the term is tuned, a modal slab runs untuned."""
+    n, N = 34, 3
+    sysm = _system(n, N, 3000 + n)
+    ref = oracle.psiN(sysm.tensors[N], n, N, sysm.U, sysm.V, sysm.lam, p1_block=8)
+    pre = [3, 17]
+    ref_slab = oracle.h_slab(sysm.tensors[N], n, N, sysm.U, sysm.V, sysm.lam, pre)
+    with npf.Plan(sysm.lam, sysm.U, sysm.V, N) as p:
+        p.set_option(npf.OPT_TILE_N, 0)
+        p.set_tensor(N, sysm.tensors[N])
+        assert rel_fro(p.modal_slab(N, pre), ref_slab) < 1e-10
+        assert rel_fro(p.term(N), ref) < 1e-10
+
+
+@pytest.mark.parametrize("n,N", [(2, 2), (2, 3), (4, 4), (128, 2)])
+def test_smallest_and_largest_systems(npf, n, N):
+    """n = 2 and 4 (one mostly padded sub-block) and n = 128, the largest system of the
+    tensor-core path (K' = 256: every chunk full, |L0| may reach 2^22)."""
+    sysm = _system(n, N, 5000 + n)
+    ref = oracle.psiN(sysm.tensors[N], n, N, sysm.U, sysm.V, sysm.lam, p1_block=8)
+    with npf.Plan(sysm.lam, sysm.U, sysm.V, N) as p:
+        p.set_tensor(N, sysm.tensors[N])
+        assert rel_fro(p.term(N), ref) < 1e-10
+
+
+def test_n128_order3_slabs(npf):
+    n, N = 128, 3
+    sysm = _system(n, N, 6000)
+    with npf.Plan(sysm.lam, sysm.U, sysm.V, N) as p:
+        p.set_tensor(N, sysm.tensors[N])
+        for pre in ([5, 127],):   # one prefix: the oracle's slab contracts the whole tensor
+            ref = oracle.h_slab(sysm.tensors[N], n, N, sysm.U, sysm.V, sysm.lam, pre)
+            assert rel_fro(p.modal_slab(N, pre), ref) < 1e-10
