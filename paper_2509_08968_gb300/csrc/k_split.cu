@@ -247,16 +247,24 @@ __device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t 
     return ((long long)a0 << 30) + (a1 << 22) + (a2 << 14) + a3;
 }
 
-// Upper bound of |V| 2^-30 = |L0 + L1 + L2 + L3| + (rounding of L3 to the V grid, 2^-31): the
-// FP32 sum plus 2^-21 of the magnitudes (three roundings of at most 2^-24 each, and the rounding
-// of the bound itself) plus 2^-30.
-__device__ __forceinline__ float level_bound(uint32_t l0, uint32_t l1, uint32_t l2, uint32_t l3)
+// A priori bound of |L2 + L3| in units of L0 (the MMAs run the pairs s + t < S): a level-l pair
+// adds at most 256 products of digits |d| <= 2^7 at weight 2^(-8l), and level l has l + 1 pairs.
+__host__ __device__ constexpr float deep_level_bound(int S)
+{
+    float b = 0.f, w = 1.f / 65536.f;   // 2^-16: level 2
+    for (int l = 2; l < S; ++l) {
+        b += (float)(l + 1) * w;
+        w *= 1.f / 256.f;
+    }
+    return b * 4194304.f * 1.001f + 1.0f;   // x 2^22, with margin
+}
+// Upper bound of |V| 2^-30 from L0 and L1 alone: their FP32 sum plus its rounding bound plus the
+// a priori bound of the deeper levels. An exponent taken from it exceeds the exact one only for
+// columns whose entries are all below ~2^9 L0 units, i.e. where the deeper levels' size matters.
+__device__ __forceinline__ float level_bound01(uint32_t l0, uint32_t l1, float deep)
 {
     const float a = __uint_as_float(l0), b = __uint_as_float(l1);
-    const float c = __uint_as_float(l2), d = __uint_as_float(l3);
-    const float s = ((a + b) + c) + d;
-    const float m = (fabsf(a) + fabsf(b)) + (fabsf(c) + fabsf(d));
-    return fmaf(m, 4.76837158203125e-07f, fabsf(s) + 9.313225746154785e-10f);   // 2^-21, 2^-30
+    return fmaf(fabsf(a) + fabsf(b), 2.384185791015625e-07f, fabsf(a + b) + deep);   // 2^-22
 }
 // e with x < 2^e <= 2x for a positive normal float x (the frexp exponent)
 __device__ __forceinline__ int f32_exponent(float x) { return ((__float_as_int(x) >> 23) & 255) - 126; }
@@ -800,10 +808,13 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const float2 sf = make_float2((float)sigma.x, (float)sigma.y);
                 const float fmb = (float)(args.invfact * mult_base);
                 if (ok) {
+                    constexpr float deep = deep_level_bound(S);
                     for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
-                        uint32_t rv[4][4], iv[4][4];
-                        load_levels<S>(trow + c4, 128, rv);
-                        load_levels<S>(trow + bnc + c4, 128, iv);
+                        uint32_t rv[2][4], iv[2][4];   // levels 0 and 1 only
+                        tc::tmem_ld4(trow + c4, rv[0]);
+                        tc::tmem_ld4(trow + c4 + 128, rv[1]);
+                        tc::tmem_ld4(trow + bnc + c4, iv[0]);
+                        tc::tmem_ld4(trow + bnc + c4 + 128, iv[1]);
                         tc::tmem_wait_ld();
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -811,9 +822,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             const int qc = qbase + cl;
                             const int eb = colEb[cl];
                             // upper bounds of |V_re|, |V_im| in units of 2^30 (V = (L0 + L1 + L2 +
-                            // L3) 2^30): the FP32 sum plus its worst rounding error
-                            const float br = level_bound(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
-                            const float bi = level_bound(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
+                            // L3) 2^30)
+                            const float br = level_bound01(rv[0][c], rv[1][c], deep);
+                            const float bi = level_bound01(iv[0][c], iv[1][c], deep);
                             const bool valid = row_ok && !no_write && qc < args.ncv &&
                                                (!args.colmask || qc <= firstp);
                             unsigned key = 0;
