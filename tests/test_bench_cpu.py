@@ -1,0 +1,64 @@
+"""Host logic of bench.py (no GPU): the DRAM-traffic record is reported only for the kernel
+sources it was captured on, both arms describe the same workload, and the algorithmic work
+counts follow their closed forms."""
+import json
+import os
+import shutil
+from math import comb
+
+import pytest
+
+import bench
+
+
+def test_traffic_record_matches_current_sources():
+    d = json.load(open(os.path.join(bench.ROOT, "profiles", "dram_split_mode_product_n120.json")))
+    assert bench.measured_traffic("split_mode_product", "n120") == d["traffic_per_launch"]
+    assert d["traffic_per_launch"] == d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]
+    assert bench.measured_traffic("split_reduce", "n120") is None      # no record
+    assert bench.measured_traffic("split_mode_product", "n60") is None
+
+
+def test_traffic_record_is_dropped_when_a_source_changes(tmp_path, monkeypatch):
+    """A copy of the tree whose kernel source differs by one byte reports no traffic."""
+    root = tmp_path / "repo"
+    d = json.load(open(os.path.join(bench.ROOT, "profiles", "dram_split_mode_product_n120.json")))
+    (root / "profiles").mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "dram_split_mode_product_n120.json"),
+                root / "profiles")
+    for src in d["sources"]:
+        dst = root / src
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, src), dst)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.measured_traffic("split_mode_product", "n120") == d["traffic_per_launch"]
+    with open(root / d["sources"][0], "ab") as f:
+        f.write(b"\n")
+    assert bench.measured_traffic("split_mode_product", "n120") is None
+
+
+def test_both_arms_share_the_workload_config():
+    ours = bench.workload_config(120, (3, 4), "split_bf16")
+    ref = bench.workload_config(120, (3, 4), "fp64 (CPU oracle)")
+    assert {k: v for k, v in ours.items() if k != "precision"} == \
+           {k: v for k, v in ref.items() if k != "precision"}
+    assert ours["entries_per_step"] == 120 ** 4 + 120 ** 5
+
+
+@pytest.mark.parametrize("n", [20, 60, 120])
+def test_algorithmic_work_closed_forms(n):
+    """Per-order counts of the tensor kernels (order 3 alone: mode products c = 1, 2)."""
+    pairs = bench.PAIRS["split_bf16"]
+    saved = bench.ORDERS
+    try:
+        bench.ORDERS = (3,)
+        up, _ = bench.algorithmic_work_per_step("split_upper_contraction", n, "split_bf16")
+        mp, kind = bench.algorithmic_work_per_step("split_mode_product", n, "split_bf16")
+        dv, _ = bench.algorithmic_work_per_step("split_mode_divide", n, "split_bf16")
+    finally:
+        bench.ORDERS = saved
+    assert kind == "flops"
+    assert up == comb(n + 2, 3) * n * n * 4 * pairs
+    # c = 1: n (i) x n (p) x n^2 (a's) x n (K) x 8; c = 2: n x C(n+1, 2) x n x n x 8
+    assert mp == (n * n * n * n * n * 8 + n * comb(n + 1, 2) * n * n * 8) * pairs
+    assert dv == n * comb(n + 2, 3) * n * 8 * pairs
