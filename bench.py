@@ -317,7 +317,14 @@ def main():
         if work is not None:
             per_launch = work * args.steps / cnt
             avg_ms = tot_ms / cnt
-            if kind == "flops":
+            if kind == "flops" and name.startswith("fp64"):
+                # FP64 pipe: the measured BF16 figure times the nominal FP64 / BF16 dense ratio
+                # of this GPU (1.25 / 2250 TFLOP/s)
+                peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0
+                achieved = per_launch / (avg_ms * 1e-3) / 1e12
+                bound, unit = "fp64", "TFLOP/s"
+                psrc = f"fp64 = bf16 sustained ({src}) x nominal FP64/BF16 ratio 1.25/2250"
+            elif kind == "flops":
                 peak = peaks.get("bf16_tflops_sustained", 1700.0)
                 achieved = per_launch / (avg_ms * 1e-3) / 1e12
                 bound, unit, psrc = "tensor", "TFLOP/s", f"bf16 sustained ({src})"
