@@ -322,7 +322,7 @@ def main():
                 # of this GPU (1.25 / 2250 TFLOP/s)
                 peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0
                 achieved = per_launch / (avg_ms * 1e-3) / 1e12
-                bound, unit = "fp64", "TFLOP/s"
+                bound, unit = "alu", "TFLOP/s"   # DFMA on the FP64 pipe
                 psrc = f"fp64 = bf16 sustained ({src}) x nominal FP64/BF16 ratio 1.25/2250"
             elif kind == "flops":
                 peak = peaks.get("bf16_tflops_sustained", 1700.0)
