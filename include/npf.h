@@ -32,7 +32,9 @@
  *   - Every call returns NPF_OK or an error code and writes nothing to the outputs on error;
  *     npf_last_error() gives a message (thread-local). No C++ exception crosses the ABI.
  *   - A handle is used by one host thread at a time. Work is issued on the handle's stream
- *     (NPF_OPT_STREAM), and every call returns after that stream has finished its work.
+ *     (NPF_OPT_STREAM), and every call returns after that stream has finished its work; only the
+ *     copies that npf_compute_prefetch starts on the handle's own upload stream outlive the call
+ *     (the next call that uses tensors waits for them).
  */
 #ifndef NPF_H_
 #define NPF_H_
