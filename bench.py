@@ -137,6 +137,7 @@ def dist_setup():
 
 def workload_config(n, orders, precision, swing=False, modes=None):
     """The `config` of a single-system workload line (both arms)."""
+    from math import comb
     return {"workload": (f"n={n} swing model ({n // 2} machines, ring + random lines), NPF orders "
                          f"{', '.join(map(str, orders))}, derivative tensors generated on the GPU")
                         if swing else
@@ -144,8 +145,26 @@ def workload_config(n, orders, precision, swing=False, modes=None):
                          f"{', '.join(map(str, orders))}, packed symmetric tensors 30% N(0,1)"),
             "n": n, "orders": list(orders), "precision": precision,
             "entries_per_step": sum((modes or n) ** (N + 1) for N in orders),
+            # distinct entries (h is symmetric in its lower indices): what the method forms
+            "unique_entries_per_step": sum((modes or n) * comb((modes or n) + N - 1, N)
+                                           for N in orders),
             "modes": modes or n,
             "l2": "inputs larger than L2 (packed order-4 tensor 8.7 GB)"}
+
+
+def fp64_equivalent(n, m, orders, ms):
+    """The whole step as the dense FP64 work of Algorithm 2: F(n, N) = 2n(4N + 6) real flops per
+    entry of the dense m^(N+1) modal tensor (one real x complex and N complex x complex products of
+    length n, and the Khatri-Rao step). The method forms only non-decreasing tuples, so this rate
+    can exceed what the GPU's FP64 or BF16 units execute: it compares with a dense FP64 code."""
+    F = {N: 2 * n * (4 * N + 6) for N in orders}
+    flops = sum(m ** (N + 1) * F[N] for N in orders)
+    tflops = flops / (ms * 1e-3) / 1e12
+    peaks, _ = measured_peaks()
+    fp64_roof = peaks.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0
+    return {"flops_per_entry": {str(N): F[N] for N in orders}, "tflops": tflops,
+            "x_fp64_roof": tflops / fp64_roof,
+            "fp64_roof_tflops": fp64_roof}
 
 
 def cpu_baseline(seconds_budget=20.0):
@@ -394,6 +413,7 @@ def main():
             "config": workload_config(n, ORDERS, args.precision, swing, m_modes),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+            "fp64_equivalent": fp64_equivalent(n, m_modes, ORDERS, ms),
         }
         print(json.dumps(line))
     if dist:
