@@ -47,21 +47,32 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def code_hash(paths):
+    """SHA-256 of source files with their comments and whitespace removed: edits that leave the
+    code itself unchanged keep the hash."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                   # line comments
+        h.update("".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def measured_traffic(kernel, workload):
     """DRAM bytes (read + write) per launch of `kernel` on `workload` from the committed ncu
     capture profiles/dram_<kernel>_<workload>.json, or None when there is none or when the kernel
-    sources no longer hash to the captured build's."""
-    import hashlib
+    sources' code no longer hashes to the captured build's."""
     p = os.path.join(ROOT, "profiles", f"dram_{kernel}_{workload}.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    h = hashlib.sha256()
-    for src in d["sources"]:
-        with open(os.path.join(ROOT, src), "rb") as f:
-            h.update(f.read())
-    return d["traffic_per_launch"] if h.hexdigest() == d["sources_sha256"] else None
+    current = code_hash([os.path.join(ROOT, src) for src in d["sources"]])
+    return d["traffic_per_launch"] if current == d["code_sha256"] else None
 
 
 class ClockSampler:

@@ -18,7 +18,8 @@
 // [Re W_0p, -Im W_0p, Re W_1p, -Im W_1p, ..] and Im-row p = [Im W_0p, Re W_0p, ..], so one real
 // GEMM yields Re and Im of X.W; a real operand row has K' = 128 plain entries.
 //
-// Dataflow of one order N (Algorithm 2), indices padded to NP = 128:
+// Dataflow of one order N (Algorithm 2), indices padded to the row radix 2^lg (32, 64 or 128,
+// at least n; see split_run):
 //   P1     : S[i][Q] = sum_j psi_{ij} A^j_Q on the packed (sorted) lower tuples Q (real rows Q,
 //            K = j), then per-i digit records of S (the upper index first: step 4 moved ahead,
 //            which the contraction order allows).
@@ -1589,7 +1590,8 @@ static void launch_rows(Plan& p, const char* name, const CUtensorMap& tA, const 
 static double factorial(int N) { double f = 1; for (int t = 2; t <= N; ++t) f *= t; return f; }
 
 // Device memory of one order: S (FP64, n x P), records (n x P x 32 B), and per i of a batch two
-// operand buffers of NP^(N-1) rows x 256 K' x S planes (BF16) plus exponents.
+// operand buffers of R^(N-1) rows x 2R K' x S planes (BF16) plus exponents, R = 2^lg the row
+// radix.
 template <int S>
 static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const double2* W)
 {

@@ -20,7 +20,8 @@ def test_traffic_record_matches_current_sources():
 
 
 def test_traffic_record_is_dropped_when_a_source_changes(tmp_path, monkeypatch):
-    """A copy of the tree whose kernel source differs by one byte reports no traffic."""
+    """A copy of the tree whose kernel code changes reports no traffic; comments and whitespace
+    do not count."""
     root = tmp_path / "repo"
     d = json.load(open(os.path.join(bench.ROOT, "profiles", "dram_split_mode_product_n120.json")))
     (root / "profiles").mkdir(parents=True)
@@ -33,7 +34,10 @@ def test_traffic_record_is_dropped_when_a_source_changes(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.measured_traffic("split_mode_product", "n120") == d["traffic_per_launch"]
     with open(root / d["sources"][0], "ab") as f:
-        f.write(b"\n")
+        f.write(b"\n// a comment\n/* and a block\n   comment */\n")
+    assert bench.measured_traffic("split_mode_product", "n120") == d["traffic_per_launch"]
+    with open(root / d["sources"][0], "ab") as f:
+        f.write(b"static int unused_marker = 0;\n")
     assert bench.measured_traffic("split_mode_product", "n120") is None
 
 
