@@ -1,7 +1,7 @@
 """The learned surrogate end to end on the operating-point family (n = 40, order 3): labels from
 the plain GPU method (checked against the CPU oracle), an ensemble of five BF16 MLPs
 4 -> 256 -> 256 -> 256 -> 64 trained by the library's kernels on 4096 points, and 512 held-out
-points judged by the plain method, with fallback to it where the members disagree by more than 5%.
+points evaluated by the plain method, with fallback to it where the members disagree by more than 5%.
 The test states what the network gains over the method without it (throughput at bounded error).
 """
 import time
