@@ -85,7 +85,7 @@ enum npf_option {
                                D = lambda_p1 + .. + lambda_pN - lambda_i exactly from FP64 inputs
                                (error-free float transformations, exact under cancellation) and
                                the quotient in double-float arithmetic (relative error ~2^-45),
-                               about 5x faster on this GPU, whose FP64 rate is ~1/900 of its
+                               about 5x faster on this GPU, whose FP64 rate is ~1/1700 of its
                                tensor rate. Both are rounded to the same 6 x 8-bit slices next. */
     NPF_OPT_DEBUG_STALL = 9   /* test hook (not for use): 1 makes the tensor-core pipeline withhold
                                its first completion signal, so a bounded device wait runs out
@@ -128,7 +128,10 @@ int npf_set_modes(npf_handle* h, const npf_c128* eigvals, const npf_c128* U, con
 int npf_set_mode_subset(npf_handle* h, int m, const int* modes);
 
 /* Copy the packed order-`order` tensor (2 <= order <= N_max; layout above; host or device) into
- * the plan's device memory. Replaces a previous tensor of that order. */
+ * the plan's device memory. Replaces a previous tensor of that order. Order 1 takes the Jacobian
+ * A1 itself (coeffs[j*n + a] = A1[j][a]); it is used only by npf_get_modal_slab(order 1), where
+ * the chain of Algorithm 2 with the divide off returns Psi A1 Phi = diag(lambda) (a check of the
+ * contraction kernels against the eigen-decomposition). */
 int npf_set_tensor(npf_handle* h, int order, const double* coeffs);
 
 /* The order-`order` derivative tensor of a multi-machine swing model, generated on the GPU into
@@ -194,7 +197,8 @@ int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out);
 int npf_get_term_rows(npf_handle* h, int order, int i_lo, int i_hi, npf_c128* out);
 
 /* One modal slab h^i_{prefix, q}: out[i*n + q] for the fixed prefix p_1..p_{N-1} (N-1 ints in
- * [0, n)), every mode i and last index q. Host or device `out`. For parity checks at full size. */
+ * [0, n)), every mode i and last index q. Host or device `out`. For parity checks at full size.
+ * Order 1 (prefix unused, may be NULL): h^i_q = (Psi A1 Phi)_{iq} / (lambda_q - lambda_i). */
 int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* out);
 
 /* Many plans in one call (independent systems of uneven size and order; the paper notes that its
@@ -237,17 +241,20 @@ int npf_get_profile(npf_handle* h, int cap, const char** names, int64_t* launche
 int64_t npf_launch_count(void);
 
 /* The order-`order` term Psi_N[i*n + k] computed by the native-FP64 kernels without allocating
- * any device memory (the paper has no counterpart: this is for callers that cannot call
- * cudaMalloc -- code running while a CUDA graph it does not own is being captured, processes held
- * to a memory pool they were given, plugins whose host application forbids device allocations).
- * Every pointer is a DEVICE pointer owned by the caller: eigvals[n], U[n*n], V[n*n] (layouts as
- * for npf_plan), coeffs = the packed order-`order` tensor, out[n*n]. eps is the clamp of
- * Algorithm 2 step 9. stream is a cudaStream_t (NULL = legacy default); the call returns after
- * the stream has finished. Scratch is one file-scope device array of 64 MiB per device (kept
- * until the process exits); a problem whose scratch does not fit (all of 2 n^N + n^(N-1) complex
- * values for one output-index batch, plus small tables) is rejected with NPF_ERR_UNSUPPORTED
- * before any work. The first call on a device looks up the array's device address (set-up, once
- * per device): make it before any stream capture. All calls share the array, so calls that
+ * any device memory. The paper has no counterpart: this entry point exists for callers that may
+ * not call cudaMalloc -- a process confined to a memory pool it was handed (allocating outside it
+ * would break the host's accounting), a plugin whose host application forbids device
+ * allocations, or a latency-bound loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree may imply. Every pointer is a DEVICE pointer owned by the caller:
+ * eigvals[n], U[n*n], V[n*n] (layouts as for npf_plan), coeffs = the packed order-`order` tensor,
+ * out[n*n]. eps is the magnitude below which a resonance denominator is replaced by the real
+ * value eps. stream is a cudaStream_t (NULL = legacy default); the call returns after the stream
+ * has finished. Scratch is one file-scope device array of 64 MiB per device (kept until the
+ * process exits); a problem whose scratch does not fit (all of 2 n^N + n^(N-1) complex values for
+ * one output-index batch, plus small tables) is rejected with NPF_ERR_UNSUPPORTED before any
+ * work. The first call on a device looks up the array's device address (set-up, once per
+ * device), so make that first call before any stream capture begins. All calls share the array
+ * and it keeps the last call's contents (every call rebuilds what it reads), so calls that
  * overlap on the GPU race on it. */
 int npf_term_fp64_noalloc(int n, int order, const npf_c128* eigvals, const npf_c128* U,
                           const npf_c128* V, const double* coeffs, double eps, npf_c128* out,

@@ -52,7 +52,8 @@ def packed_tensor(model, N):
 
 
 def finite_difference_tensor(model, N, h=1e-3):
-    """Central-difference estimate of the packed order-N tensor (N = 2 or 3), from f alone."""
+    """Central-difference estimate of the packed order-N tensor from f alone (step h; error
+    O(h^2) plus rounding O(eps / h^N))."""
     m = model.m
     n = 2 * m
     x0 = np.concatenate([model.delta, np.zeros(m)])

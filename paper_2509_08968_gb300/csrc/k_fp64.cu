@@ -273,6 +273,23 @@ void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out)
     double2* X = (double2*)ar.base;
     double2* Y = X + (size_t)n * nN1;
     DivideArgs none = divide_args(p, N);
+    if (N == 1) {
+        // order 1: X[p][j] = sum_a A1[j][a] phi_{a p}, then h[i][p] = sum_j psi_ij X[p][j] / D
+        ar.reserve((size_t)n * n * sizeof(double2));
+        X = (double2*)ar.base;
+        {
+            LaunchScope ls(&p.prof, "fp64_first_contraction", p.stream);
+            k64_first<<<(unsigned)((n + 127) / 128), 128, 0, p.stream>>>(
+                n, 1, p.d_tensor[1], p.packed_count[1], p.d_cnt, p.d_U, 0, n, X);
+            NPF_CUDA(cudaGetLastError());
+        }
+        DivideArgs da = divide_args(p, 1);
+        da.ndig = 0;
+        da.nlast = n;
+        da.off_last = 0;
+        gemm(p, "fp64_psi_divide", X, n, n, p.d_Vt, n, n, d_out, 2, da);
+        return;
+    }
     {
         LaunchScope ls(&p.prof, "fp64_first_contraction", p.stream);
         const int64_t tot = (int64_t)n * nN1;
@@ -303,10 +320,10 @@ void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out)
 }
 
 // ---------------------------------------------------------------------------------------
-// Allocation-free variant of the order-N term, for callers that cannot call cudaMalloc: code
-// that runs while a CUDA graph it does not own is being captured, processes that must stay
-// inside a memory pool handed to them, or plugins whose host application forbids device
-// allocations. Its scratch is the file-scope array below, NOALLOC_SCRATCH_BYTES per device,
+// Allocation-free variant of the order-N term, for callers that may not call cudaMalloc:
+// processes that must stay inside a memory pool handed to them, plugins whose host application
+// forbids device allocations, or latency-bound loops that cannot take the device-wide
+// synchronisation an allocation may imply. Its scratch is the file-scope array below, NOALLOC_SCRATCH_BYTES per device,
 // which every device that loads this library keeps until the process exits. Host code must not
 // pass `g_noalloc_scratch` itself to a kernel (on the host that name is only a stand-in); the
 // device address comes from cudaGetSymbolAddress, looked up once per device by the first call

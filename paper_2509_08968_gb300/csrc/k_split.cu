@@ -691,7 +691,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     }
                 }
                 if (args.rp >= 1) firstp = dg[0];
-                if (SUBB) row_ok &= outer < args.nouter;
+                // rows past the batch: sub-blocks, and order 1 (one row per upper index)
+                if (SUBB || args.R == 1) row_ok &= outer < args.nouter;
             }
 
             // rows of the swapped pair of shared a's (digits rp, rp + 1 when both are shared):
@@ -1782,7 +1783,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
 
 static void split_any(Plan& p, int N, double2* d_out, const int* prefix, const double2* W)
 {
-    if (N < 2) fail(NPF_ERR_ARG, "order must be >= 2");
+    if (N < 1 || (N == 1 && !prefix)) fail(NPF_ERR_ARG, "order must be >= 2 (order 1: modal slabs only)");
     if (N > 4) fail(NPF_ERR_UNSUPPORTED, "the tensor-core path supports orders <= 4 (use NPF_PREC_FP64)");
     switch (default_slices(p)) {
     case 2: split_run<2>(p, N, d_out, prefix, W); break;

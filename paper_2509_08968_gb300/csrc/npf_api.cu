@@ -540,6 +540,7 @@ npf_handle* npf_plan(int n, int N_max, const npf_c128* eigvals, const npf_c128* 
         NPF_CUDA(cudaMalloc(&p.d_tmp, nn * sizeof(double2)));
         NPF_CUDA(cudaMalloc(&p.d_perm, n * sizeof(int)));
         p.nm = n;
+        p.packed_count[1] = n;   // an order-1 tensor is the Jacobian A1[j][a] (modal slabs only)
         for (int N = 2; N <= N_max; ++N) {
             NPF_CUDA(cudaMalloc(&p.d_psiN[N], nn * sizeof(double2)));
             p.packed_count[N] = npf::packed_count(n, N);
@@ -598,7 +599,7 @@ int npf_set_tensor(npf_handle* h, int order, const double* coeffs)
     return guarded([&] {
         if (!h || !coeffs) npf::fail(NPF_ERR_ARG, "null handle or coeffs");
         Plan& p = h->p;
-        if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        if (order < 1 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [1, N_max]");
         activate_staged(p);
         const size_t bytes = (size_t)p.n * p.packed_count[order] * sizeof(double);
         const void* before[2] = {p.d_tensor[order], npf::split_tensor_planes(p, order)};
@@ -637,7 +638,7 @@ int npf_get_tensor(npf_handle* h, int order, double* out)
         if (!h || !out) npf::fail(NPF_ERR_ARG, "null argument");
         Plan& p = h->p;
         activate_staged(p);
-        if (order < 2 || order > p.Nmax || !p.d_tensor[order])
+        if (order < 1 || order > p.Nmax || !p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));
         NPF_CUDA(cudaMemcpyAsync(out, p.d_tensor[order],
                                  (size_t)p.n * p.packed_count[order] * sizeof(double),
@@ -781,7 +782,7 @@ int npf_get_modal_slab(npf_handle* h, int order, const int* prefix, npf_c128* ou
     return guarded([&] {
         if (!h || !out || (!prefix && order > 1)) npf::fail(NPF_ERR_ARG, "null argument");
         Plan& p = h->p;
-        if (order < 2 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [2, N_max]");
+        if (order < 1 || order > p.Nmax) npf::fail(NPF_ERR_ARG, "order must be in [1, N_max]");
         activate_staged(p);
         if (!p.d_tensor[order])
             npf::fail(NPF_ERR_MISSING_TENSOR, "no tensor set for order " + std::to_string(order));

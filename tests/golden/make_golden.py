@@ -3,9 +3,16 @@
 Calls only the CPU oracle (oracle/) on the seeded synthetic inputs of npf_synth:
   n120_seed0_order3.npz : Psi_3[i, k] for the n = 120 block-structured system (seed 0),
                           the full order-3 correction term of Eq. 7.
-Run from the repository root:  python tests/golden/make_golden.py [order4]
-  n60_seed2_order4.npz  : Psi_4 of the n = 60 system (seed 2).
-  n120_seed0_order4_slabs.npz : three order-4 modal slabs of the n = 120 system (seed 0).
+Run from the repository root:  python tests/golden/make_golden.py [order4 | radix128 | n120order4]
+  order4:
+    n60_seed2_order4.npz  : Psi_4 of the n = 60 system (seed 2).
+    n120_seed0_order4_slabs.npz : three order-4 modal slabs of the n = 120 system (seed 0).
+  radix128 (systems with 64 < n <= 128, whose digits use the row radix 128):
+    n68_seed0_order4.npz  : Psi_4 of the n = 68 system (seed 0), ~10 min on 8 cores.
+    n80_seed1_order4.npz  : Psi_4 of the n = 80 system (seed 1), ~25 min on 8 cores.
+  n120order4:
+    n120_seed0_order4.npz : Psi_4 of the n = 120 system (seed 0), the full order-4 term of the
+                            benchmarked system, ~3-4 h on 8 cores.
 """
 import os
 import sys
@@ -30,7 +37,7 @@ def main():
     print(f"n120 order 3: {time.time() - t:.1f} s, |Psi_3|_F = {np.linalg.norm(psi3):.6e}")
 
 
-if __name__ == "__main__" and "order4" not in sys.argv:
+if __name__ == "__main__" and len(sys.argv) == 1:
     main()
 
 
@@ -55,3 +62,31 @@ SLABS_120 = [(0, 0), (33, 91), (119, 64)]
 
 if __name__ == "__main__" and "order4" in sys.argv:
     order4()
+
+
+def radix128():
+    """Full Psi_4 of two systems above 64 states (n = 68 seed 0, n = 80 seed 1)."""
+    for n, seed in ((68, 0), (80, 1)):
+        sysm = S.config_blocks(n, seed, orders=(4,))
+        t = time.time()
+        psi4 = oracle.psiN(sysm.tensors[4], n, 4, sysm.U, sysm.V, sysm.lam, p1_block=1)
+        np.savez_compressed(os.path.join(HERE, f"n{n}_seed{seed}_order4.npz"), psi4=psi4)
+        print(f"n{n} order 4: {time.time() - t:.1f} s, |Psi_4|_F = {np.linalg.norm(psi4):.6e}",
+              flush=True)
+
+
+def n120_order4():
+    """Full Psi_4 of the n = 120 system (seed 0)."""
+    sysm = S.config_n120(0, orders=(4,))
+    t = time.time()
+    psi4 = oracle.psiN(sysm.tensors[4], 120, 4, sysm.U, sysm.V, sysm.lam, p1_block=1)
+    np.savez_compressed(os.path.join(HERE, "n120_seed0_order4.npz"), psi4=psi4)
+    print(f"n120 order 4: {time.time() - t:.1f} s, |Psi_4|_F = {np.linalg.norm(psi4):.6e}",
+          flush=True)
+
+
+if __name__ == "__main__" and "radix128" in sys.argv:
+    radix128()
+
+if __name__ == "__main__" and "n120order4" in sys.argv:
+    n120_order4()

@@ -1,7 +1,7 @@
 """Split-BF16 tensor-core path (and its FP32-level form) against the CPU oracle.
 
 Bars from the specification of the path: relative Frobenius error <= 1e-10 for the FP64-emulating
-split form (5 BF16 slices) and <= 1e-5 for the FP32 form (3 slices), for h slabs, Psi_N and NPF.
+split form (6 BF16 slices) and <= 1e-5 for the FP32 form (3 slices), for h slabs, Psi_N and NPF.
 """
 import math
 import os
@@ -178,3 +178,46 @@ def test_fp64_quotient_option_agrees(npf):
             out[q] = p.term(3)
         assert rel_fro(out[q], ref) < TOL["split_bf16"], (q, rel_fro(out[q], ref))
     assert rel_fro(out[0], out[1]) < 1e-11
+
+
+def _gold(name):
+    return os.path.join(os.path.dirname(__file__), "golden", name)
+
+
+@pytest.mark.parametrize("n,seed", [(68, 0), (80, 1)])
+def test_order4_radix128_against_stored_oracle(npf, n, seed):
+    """Order 4 above 64 states takes the row radix 128: the kernel variant without sub-blocks,
+    the mirrored first contraction, the divide epilogue with the multiplicity weights and the
+    reduction epilogue, all compared in full with the oracle's Psi_4 (term) and NPF (compute).
+    A forced budget of three upper indices per batch runs 23 batches at n = 68."""
+    path = _gold(f"n{n}_seed{seed}_order4.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    sysm = S.config_blocks(n, seed, orders=(4,))
+    ref = np.load(path)["psi4"]
+    ref_npf = oracle.npf(sysm.U, sysm.V, ref)
+    for prec in ("split_bf16", "fp32"):
+        with make_plan(npf, sysm, 4, prec) as p:
+            assert rel_fro(p.term(4), ref) < TOL[prec], (prec, rel_fro(p.term(4), ref))
+            assert rel_fro(p.compute(4), ref_npf) < TOL[prec]
+    if n == 68:
+        P = S.packed_count(n, 4)
+        per_i = 2 * (128 ** 3 * 2 * 128 * 2 * 6 + 128 ** 3 * 4) + 4096
+        budget = n * ((P + 127) // 128 * 128) * 16 + n * P * 32 + 3 * per_i + (1 << 20)
+        with make_plan(npf, sysm, 4, "split_bf16") as p:
+            p.set_option(npf.OPT_MEM_BUDGET, budget)
+            assert rel_fro(p.term(4), ref) < TOL["split_bf16"]
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_n120_orders34_against_stored_oracle(npf, prec):
+    """The benchmarked call, npf_compute(order 4) on the n = 120 system with the order-3 and
+    order-4 tensors, against the oracle's full Psi_3 and Psi_4 (stored)."""
+    g3, g4 = _gold("n120_seed0_order3.npz"), _gold("n120_seed0_order4.npz")
+    if not (os.path.exists(g3) and os.path.exists(g4)):
+        pytest.skip("golden files not generated")
+    sysm = S.config_n120(0, orders=(3, 4))
+    psi3, psi4 = np.load(g3)["psi3"], np.load(g4)["psi4"]
+    with make_plan(npf, sysm, 4, prec) as p:
+        assert rel_fro(p.term(4), psi4) < TOL[prec]
+        assert rel_fro(p.compute(4), oracle.npf(sysm.U, sysm.V, psi3 + psi4)) < TOL[prec]

@@ -79,6 +79,12 @@ def test_surrogate_gain_over_plain_method(setup):
     assert np.all(rel[fb] < 1e-9)
     # the gate tracks the error: rows it rejects are worse than rows it accepts
     assert np.median(rowmax[fb]) > np.median(rowmax[~fb])
+    # gate misses: accepted rows whose worst output is off by more than the 5% gate. The spread
+    # of five members estimates the error, so a few misses are expected; they stay rare and
+    # bounded (one accepted row of 512 at 13% was measured)
+    miss = rowmax[~fb] > 0.05
+    assert miss.mean() <= 0.02, miss.mean()
+    assert rowmax[~fb].max() < 0.25, rowmax[~fb].max()
     # the gain: queries per second against the plain method on the same points
     assert 512 / t_sur > 100 * (512 / t_plain)
     assert 512 / t_gated > 3 * (512 / t_plain)

@@ -10,7 +10,9 @@ Khatri-Rao orientation):
 * the collapse identity with the divide disabled (a closed form at any size);
 * invariance of the NPFs under eigenvector rescaling, and the matching scaling of h;
 * symmetry of h in the lower indices; the identity-eigenvector case; the eps clamp;
-* brute force (Eq. 4 and the Psi_N sum written out literally) against the factorised forms.
+* brute force (Eq. 4 and the Psi_N sum written out literally) against the factorised forms;
+* the contraction chain run on A1 as an order-1 tensor with the divide off: Psi A1 Phi =
+  diag(lambda), which the eigen-decomposition of the generator fixes.
 """
 import itertools
 import math
@@ -231,3 +233,23 @@ def test_npf_orders_cumulative():
     S2 = oracle.psiN(sysm.tensors[2], 10, 2, sysm.U, sysm.V, sysm.lam)
     S3 = oracle.psiN(sysm.tensors[3], 10, 3, sysm.U, sysm.V, sysm.lam)
     np.testing.assert_allclose(P3, sysm.U * (sysm.V + S2 + S3).T, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("n,seed", [(4, 0), (10, 1), (20, 2)])
+def test_order1_chain_gives_eigenvalues(n, seed):
+    """The chain of Algorithm 2 (lower index with Phi, upper index with Psi, 1/1!) applied to the
+    Jacobian A1 as an order-1 tensor, with the divide off, gives Psi A1 Phi = diag(lambda): the
+    generator builds A1 = P B P^-1 with U = P W, so this is fixed by the eigen-decomposition, not
+    by the oracle. A transposed Phi or Psi, or a wrong pairing of the upper index, breaks it."""
+    sysm = S.modal_system(n, seed) if n % 4 else S.config_blocks(n, seed, orders=())
+    A1 = np.ascontiguousarray(sysm.A1)           # packed order 1: coeffs[j, a] = A1[j, a]
+    h = oracle.h_fact(A1, n, 1, sysm.U, sysm.V, sysm.lam, divide=False)
+    assert h.shape == (n, n)
+    scale = np.abs(sysm.lam).max()
+    np.testing.assert_allclose(h, np.diag(sysm.lam), rtol=0, atol=1e-12 * scale)
+    if n <= 10:
+        hb = oracle.h_brute(A1, sysm.U, sysm.V, sysm.lam, divide=False)
+        np.testing.assert_allclose(hb, np.diag(sysm.lam), rtol=0, atol=1e-12 * scale)
+    # with the divide on, D = lambda_p - lambda_i: zero on the diagonal, clamped to eps (step 9)
+    hd = oracle.h_fact(A1, n, 1, sysm.U, sysm.V, sysm.lam)
+    np.testing.assert_allclose(np.diag(hd), sysm.lam / oracle.DEFAULT_EPS, rtol=1e-6)

@@ -28,6 +28,20 @@ def test_closed_form_tensors_match_finite_differences():
         assert np.count_nonzero(A[:3]) == 0            # angle equations are linear
 
 
+def test_order4_closed_form_matches_richardson_differences():
+    """Order 4: the central difference of step h has an O(h^2) error and an O(eps / h^4)
+    rounding error, so one Richardson step, (4 D(h/2) - D(h)) / 3, removes the h^2 term and
+    leaves ~1e-8 at h = 0.02."""
+    for m, seed in ((2, 0), (3, 1)):
+        mod = S.swing_model(m, seed)
+        A = swing.packed_tensor(mod, 4)
+        h = 2e-2
+        F = (4 * swing.finite_difference_tensor(mod, 4, h / 2)
+             - swing.finite_difference_tensor(mod, 4, h)) / 3
+        assert np.count_nonzero(A) > 0
+        assert np.abs(A - F).max() < 1e-6 * np.abs(A).max(), m
+
+
 def test_zero_mode_of_the_rotational_symmetry():
     """Without reference-bus lines, shifting every angle by the same amount leaves f unchanged,
     so A1 has the eigenvector (1, .., 1, 0, .., 0) with eigenvalue 0; the lines remove it."""

@@ -1,11 +1,13 @@
 """The allocation-free entry point npf_term_fp64_noalloc, called through the C ABI.
 
-Some callers cannot allocate device memory (code running while a CUDA graph they do not own is
-being captured, processes confined to a memory pool, plugins whose host forbids cudaMalloc). For
-them the library offers one entry point whose scratch is a fixed 64 MiB device array. This test
-checks its output against the allocating entry point (npf_plan + npf_get_term, native FP64) on two
-calls in a row with different sizes, so that the second call runs on the array as the first one
-left it, and checks that a problem too large for the array is rejected.
+Some callers may not allocate device memory: a process confined to a memory pool it was handed, a
+plugin whose host application forbids cudaMalloc, a latency-bound loop that cannot take the
+device-wide synchronisation an allocation may imply. For them the library offers one entry point
+whose scratch is a fixed 64 MiB device array. This test checks its output against the CPU oracle
+and against the allocating entry point (npf_plan + npf_get_term, native FP64) on consecutive calls
+with different sizes, so that each call runs on the array as the previous one left it; one case
+(n = 30, order 4) needs two output-index batches per pass through the array. It also checks that a
+problem too large for the array is rejected.
 """
 import ctypes
 
@@ -13,6 +15,7 @@ import numpy as np
 import pytest
 
 import npf_synth as S
+import oracle
 from tests._util import rel_fro
 
 pytestmark = pytest.mark.gpu
@@ -53,15 +56,23 @@ def _reference_term(npf, sysm, N):
         return p.term(N)
 
 
-def test_noalloc_matches_allocating_entry_point_twice(lib):
+def _system_n30():
+    sysm = S.modal_system(30, 7)
+    sysm.tensors[4] = S.random_packed_tensor(30, 4, 7)
+    return sysm
+
+
+def test_noalloc_matches_oracle_and_allocating_entry_point(lib):
     npf, L = lib
-    first = S.config_blocks(20, 5, orders=(3,))
-    second = S.config_small(1, orders=(2, 3))
-    for sysm, N in ((first, 3), (second, 3)):
+    cases = ((S.config_blocks(20, 5, orders=(3,)), 3),
+             (_system_n30(), 4),                      # 2 batches of p_1 per pass (26 MB each)
+             (S.config_small(1, orders=(2, 3)), 3))
+    for sysm, N in cases:
         got = _noalloc_term(npf, L, sysm, N)
-        ref = _reference_term(npf, sysm, N)
         assert np.isfinite(got).all()
-        assert rel_fro(got, ref) < TOL
+        ref = oracle.psiN(sysm.tensors[N], sysm.n, N, sysm.U, sysm.V, sysm.lam)
+        assert rel_fro(got, ref) < TOL, (sysm.n, N)
+        assert rel_fro(got, _reference_term(npf, sysm, N)) < TOL, (sysm.n, N)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(lib):
