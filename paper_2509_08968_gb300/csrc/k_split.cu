@@ -658,8 +658,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         const int grp = (warp - 2) / 4;                     // column group (EPI_WARPS / 4 groups)
         const int rl = q4 * 32 + lane;                      // local row within the tile
         const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
-        const int cols = bnc / (EPI_WARPS / 4);             // >= 4 for bnc >= 16
-        const int cbeg = grp * cols;
+        constexpr int NGRP = EPI_WARPS / 4;                 // column groups per lane quarter
         const int N = args.N, n = args.n;
         uint32_t t = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -676,6 +675,25 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             const int64_t rperq = args.R >> lg;
             const int kpos = rl & ((1 << lg) - 1);            // ... and the K position in it
             const int sb = rl >> lg;                          // sub-block of the tile (warp-uniform)
+            // columns of this tile that any row uses: below the modes in use and, with the
+            // sorted-tuple mask, at most the largest leading p of the tile's sub-blocks. Columns
+            // past them are neither read nor written (the rows they would fill are never used),
+            // so the column groups split only the used ones, in units of 4.
+            int vcols = min(bnc, args.ncv - qbase);
+            if (args.colmask && args.digits && args.rp >= 1 && N - 1 >= 2) {
+                // the leading p is a shared digit (for N - 1 = 1 it is the innermost one and
+                // takes every value within a sub-block)
+                int pmax = 0;
+                for (int b = 0; b < (NP >> lg); ++b) {
+                    int d0[8];
+                    row_digits((row0 + ((int64_t)b << lg)) % args.R, N - 1, lg, d0);
+                    pmax = max(pmax, d0[0]);
+                }
+                vcols = min(vcols, pmax - qbase + 1);
+            }
+            const int units = (max(vcols, 0) + 3) / 4;
+            const int cbeg = 4 * ((grp * units) / NGRP);
+            const int cols = 4 * (((grp + 1) * units) / NGRP) - cbeg;
 
             // row digits: the first rp are p's (must be in order and < n), then a's (< n)
             int dg[8];
@@ -1653,7 +1671,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     __nv_bfloat16* T[2] = {(__nv_bfloat16*)take(tbytes), (__nv_bfloat16*)take(tbytes)};
     int* E[2] = {(int*)take(ebytes), (int*)take(ebytes)};
 
-    if (!slab) launch_zero(p, d_out, (int64_t)n * n);
+    // a slab entry whose accumulator is exactly zero is not stored, so the slab starts at zero
+    launch_zero(p, d_out, (int64_t)n * n);
 
     const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, bnc);
     const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, bnc);
