@@ -7,8 +7,11 @@ entries = n^4 + n^5 per step (every h^i_{p_1..p_N} of both orders, counted dense
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision P]
 
-Multi-GPU (torchrun, one process per GPU): each rank computes its own system (seed = rank),
-no collective on the data path ("scaling": "weak"); value = all ranks' entries / max time.
+Multi-GPU (torchrun, one process per GPU): by default the upper-index rows of the one n = 120
+system are split over the ranks (paper_2509_08968_gb300.shard.sharded_npf: each rank forms its rows
+of Psi_3 and Psi_4, one NCCL all-reduce of the n x n terms, the NPF finish), "scaling": "strong";
+with --replicas each rank computes its own system (seed = rank) with no collective on the data
+path, "scaling": "weak". value = all ranks' entries / max time.
 """
 from __future__ import annotations
 
@@ -283,6 +286,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="multi-GPU: one independent system per rank (weak scaling) instead of the "
+                         "row-sharded system")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the native-FP64 comparison and the DGEMM peak measurement")
     ap.add_argument("--cpu-sample", type=float, default=0.0, help=argparse.SUPPRESS)
@@ -324,11 +330,14 @@ def main():
     global N_STATES, ORDERS
     N_STATES, ORDERS = WORKLOADS[args.workload]
     swing = args.workload.startswith("swing")
+    # several GPUs: the rows of one system split over the ranks, unless replicas are asked for
+    sharded = world > 1 and not args.replicas and not args.modes
+    seed = 0 if sharded else rank
     if swing:   # tensors generated on the GPU from a 60-machine swing model
-        model = S.swing_model(N_STATES // 2, rank)
+        model = S.swing_model(N_STATES // 2, seed)
         sysm = S.swing_system(model)
     else:
-        sysm = S.config_blocks(N_STATES, rank, orders=ORDERS)
+        sysm = S.config_blocks(N_STATES, seed, orders=ORDERS)
     n = sysm.n
     stream = torch.cuda.current_stream()
     plan = npf.Plan(sysm.lam, sysm.U, sysm.V, max(ORDERS), precision=args.precision,
@@ -350,9 +359,14 @@ def main():
         for N in ORDERS:
             plan.set_tensor(N, dev_tensors[N])
     out = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    from paper_2509_08968_gb300 import shard
+    lo, hi = shard.row_ranges(n, world)[rank] if sharded else (0, n)
 
     def step():
-        plan.compute(max(ORDERS), out)
+        if sharded:
+            shard.sharded_npf(plan, ORDERS, dist, out=out)
+        else:
+            plan.compute(max(ORDERS), out)
 
     for _ in range(args.warmup):
         step()
@@ -383,6 +397,8 @@ def main():
     plan.set_option(npf.OPT_PROFILE, 0)
     m_modes = len(subset) if subset is not None else n
     ents_rank = sum(m_modes ** (N + 1) for N in ORDERS)   # h^i_p with i, p in the modes used
+    if sharded:
+        ents_rank = ents_rank * (hi - lo) // n             # this rank's upper indices i
     ms, ents = aggregate(dist, ms, ents_rank)
     value = ents / (ms * 1e-3)
 
@@ -451,6 +467,12 @@ def main():
                    "during step s (npf_compute_prefetch); the first step's upload is not hidden")
 
             def e2e_run(k):
+                if sharded:   # every rank uploads the whole tensors and forms its rows
+                    for _ in range(k):
+                        for N in ORDERS:
+                            plan.set_tensor(N, host_t[N])
+                        shard.sharded_npf(plan, ORDERS, dist, out=host_out)
+                    return
                 for N in ORDERS:
                     plan.set_tensor(N, host_t[N])
                 for s_ in range(k):
@@ -465,6 +487,9 @@ def main():
         e2e_run(steps_e2e)
         torch.cuda.synchronize()
         dt, e_all = aggregate(dist, (time.perf_counter() - t0) / steps_e2e, ents_rank)
+        if sharded:
+            h2d, d2h = h2d * world, d2h * world
+            how = "per step: every rank uploads the packed tensors from pinned host memory"
         e2e = {"value": e_all / dt, "unit": "entries/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,
                "steps": steps_e2e, "inputs": how}
@@ -475,13 +500,19 @@ def main():
         cpu["one_core"] = cpu_baseline_one_core()
 
     if rank == 0:
+        config = workload_config(n, ORDERS, args.precision, swing, m_modes)
+        config["parallelism"] = (f"rows of one system over {world} GPUs, one NCCL all-reduce of the "
+                                 f"n x n terms per step" if sharded else
+                                 f"{world} independent systems (one per GPU)" if world > 1 else
+                                 "one GPU")
         line = {
             "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+            "vs_baseline": None,
             "dtype": DTYPES[args.precision],
             "data": "synthetic",
-            "config": workload_config(n, ORDERS, args.precision, swing, m_modes),
+            "config": config,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
             "fp64_equivalent": fp64_equivalent(n, m_modes, ORDERS, ms),
@@ -776,9 +807,9 @@ def run_surrogate(args, world, rank, local, dist):
     return 0
 
 
-DTYPES = {"split_bf16": "bf16x6-split (fp64-emulating)", "fp32": "bf16x3-split", "fp64": "f64"}
-PAIRS = {"split_bf16": 21, "fp32": 6, "fp64": 1}     # BF16 slice pairs s + t < S (S = 6 / 3)
-SLICES = {"split_bf16": 6, "fp32": 3, "fp64": 0}
+DTYPES = {"split_bf16": "bf16x6-split (fp64-emulating)", "fp32": "bf16x4-split", "fp64": "f64"}
+PAIRS = {"split_bf16": 21, "fp32": 10, "fp64": 1}    # BF16 slice pairs s + t < S (S = 6 / 4)
+SLICES = {"split_bf16": 6, "fp32": 4, "fp64": 0}
 
 
 def a_part(n, N, c):

@@ -70,7 +70,7 @@ enum npf_option {
     NPF_OPT_EPS = 1,        /* resonance clamp eps of Alg. 2 step 9 (default 1e-8; > 0). */
     NPF_OPT_STREAM = 2,     /* cudaStream_t, passed as its integer value (0 = legacy default). */
     NPF_OPT_SLICES = 3,     /* BF16 slices per operand on the split paths (2..6). Defaults: 6 for
-                               NPF_PREC_SPLIT_BF16, 3 for NPF_PREC_FP32. */
+                               NPF_PREC_SPLIT_BF16, 4 for NPF_PREC_FP32. */
     NPF_OPT_DIVIDE = 4,     /* 1 (default): divide by the resonance denominators. 0: D = 1, a
                                debugging switch behind the collapse identity
                                sum_p C^i_p prod_m psi_{p_m k} = (1/N!) sum_j psi_ij A^j_{k..k}. */
@@ -101,7 +101,8 @@ enum npf_precision {
     NPF_PREC_FP64 = 0,        /* native FP64 (CUDA-core DFMA) contraction */
     NPF_PREC_SPLIT_BF16 = 1,  /* FP64-emulating BF16 slices on tcgen05 tensor cores, FP32
                                  accumulation in TMEM, exact fixed-point recombination */
-    NPF_PREC_FP32 = 2         /* the same tensor-core kernels with 3 slices (FP32-level error) */
+    NPF_PREC_FP32 = 2         /* the same tensor-core kernels with 4 slices: relative error within
+                                 1e-5 (3 slices, FP32's 24 bits, reach 2e-5 at order 4, n = 80) */
 };
 
 /* Create a plan for an n-state system with Taylor orders up to N_max (1..6).
@@ -188,6 +189,13 @@ int npf_get_term(npf_handle* h, int order, npf_c128* out);
  * has no tensor). Summed over i and M they reproduce x^k(0) = delta up to O(delta^3) (Eq. 6).
  * out: [order][n][n], host or device. The plan's Psi_M terms and NPF buffer are overwritten. */
 int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out);
+
+/* The NPF of Algorithm 2 step 20 from given correction terms: out[k*n + i] =
+ * phi_{k i} (psi_{i k} + sum_{t < count} terms[t*n*n + i*n + k]), terms being Psi_N arrays as
+ * npf_get_term and npf_get_term_rows return them (e.g. the sum over ranks of row-sharded terms);
+ * count = 0 gives the linear PFs. terms and out host or device. Not available with a mode subset
+ * (NPF_ERR_UNSUPPORTED). */
+int npf_finish_terms(npf_handle* h, int count, const npf_c128* terms, npf_c128* out);
 
 /* Rows i_lo <= i < i_hi of Psi_N (out[i*n + k], the other rows zero; host or device): the upper
  * index is independent across rows (Eq. 7 sums over the lower indices only), so disjoint row

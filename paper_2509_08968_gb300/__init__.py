@@ -76,6 +76,7 @@ def load():
     lib.npf_get_modal_slab.argtypes = [vp, ci, vp, vp]
     lib.npf_interaction.argtypes = [vp, ci, cd, vp]
     lib.npf_get_term_rows.argtypes = [vp, ci, ci, ci, vp]
+    lib.npf_finish_terms.argtypes = [vp, ci, vp, vp]
     lib.npf_set_tensor_swing.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp, vp]
     lib.npf_get_tensor.argtypes = [vp, ci, vp]
     lib.npf_batch_compute.argtypes = [ci, vp, vp, vp]
@@ -238,6 +239,18 @@ class Plan:
         if out is None:
             out = np.empty((self.n, self.n), dtype=np.complex128)
         _check(load().npf_get_term_rows(self._h, order, int(i_lo), int(i_hi), _ptr(out)))
+        self._prefetched = []
+        return out
+
+    def finish_terms(self, terms, out=None):
+        """NPF from given correction terms (Alg. 2 step 20): `terms` is one Psi_N array [n, n]
+        or a stack [count, n, n] (NumPy or CUDA torch, complex128)."""
+        if not _is_torch(terms):
+            terms = np.ascontiguousarray(np.asarray(terms, dtype=np.complex128))
+        count = 1 if len(terms.shape) == 2 else int(terms.shape[0])
+        if out is None:
+            out = np.empty((self.n, self.n), dtype=np.complex128)
+        _check(load().npf_finish_terms(self._h, count, _ptr(terms), _ptr(out)))
         self._prefetched = []
         return out
 

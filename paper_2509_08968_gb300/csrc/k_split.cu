@@ -52,7 +52,7 @@
 namespace npf {
 
 constexpr int NP = 128;        // padded index extent (n <= 128 on this path)
-constexpr int BK = 32;         // K' elements per pipeline chunk (64 bytes, SWIZZLE_64B)
+constexpr int KSTEP = 16;      // K' elements of one MMA (BF16, 32 bytes)
 constexpr int KP = 256;        // K' of a complex operand row (interleaved Re/Im)
 constexpr int EXP_NONE = -4096;
 constexpr int TMEM_COLS = 512;
@@ -274,17 +274,26 @@ __device__ __forceinline__ int f32_exponent(float x) { return ((__float_as_int(x
 template <int S>
 struct Lev { static constexpr int N = S < 4 ? S : 4; };
 
-// Load 4 columns of every used level of one accumulator group (levels `stride` columns apart).
-template <int S>
-__device__ __forceinline__ void load_levels(uint32_t taddr, int stride, uint32_t (&v)[4][4])
+// Load 4 columns of every used level of one accumulator group (levels `stride` columns apart);
+// with the level-3 hold (HOLD), level 3 comes from shared memory (`held`) instead of TMEM.
+template <int S, bool HOLD>
+__device__ __forceinline__ void load_levels(uint32_t taddr, int stride, uint32_t (&v)[4][4],
+                                            const float4* held)
 {
 #pragma unroll
     for (int L = 0; L < 4; ++L) {
-        if (L < Lev<S>::N) tc::tmem_ld4(taddr + L * stride, v[L]);
-        else {
+        if (L < Lev<S>::N && !(HOLD && L == 3)) tc::tmem_ld4(taddr + L * stride, v[L]);
+        else if (!(HOLD && L == 3)) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) v[L][c] = 0u;
         }
+    }
+    if (HOLD) {
+        const float4 h = *held;
+        v[3][0] = __float_as_uint(h.x);
+        v[3][1] = __float_as_uint(h.y);
+        v[3][2] = __float_as_uint(h.z);
+        v[3][3] = __float_as_uint(h.w);
     }
 }
 
@@ -366,10 +375,18 @@ __global__ void k_prep_at(const double* __restrict__ A, int64_t P, int n,
 // ---------------------------------------------------------------------------------------
 enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3, EPI_REDUCE = 4 };
 
+// Tensor maps of one operand: every slice plane in one box (`all`), and the planes of levels
+// 0..2 only (`low`, the second pass of a tile with the level-3 hold).
+struct TMaps {
+    CUtensorMap all, low;
+};
+
 struct RowArgs {
     int a_rows;          // rows per plane in the A tensor map
-    int kch;             // K' chunks of 32
-    int klast;           // 16-wide K' steps in the last chunk (1 or 2): the rest is padding
+    int kch;             // pipeline stages of K' (16 or 32 wide; K' past the operands' length is
+                         // zero on both sides)
+    int klast;           // 16-wide steps in the last stage (1 or 2 for 32-wide stages): the rest
+                         // is padding
     const int* ea;       // row exponents, indexed by (local row) >> ea_shift
     int ea_shift;
     const int* eb;       // column exponents of the fixed matrix (256 entries)
@@ -419,17 +436,36 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-template <int S>
+// Pipeline of one k_rows variant. With four levels, the divide and reduction tiles run in two
+// passes with the level-3 hold (their epilogues outlast their MMAs, so the overlap pays): stages of
+// one 16-wide K' step (32-byte swizzle) to make room for the 64 KB hold. The other modes run one
+// pass over stages of two K' steps (64-byte swizzle): their MMA phase already moves operands as
+// fast as TMA refills shared memory, and a second pass would re-read planes 0..2.
+template <int S, int MODE>
+struct Pipe {
+    static constexpr bool two = Lev<S>::N == 4 && (MODE == EPI_DIVIDE || MODE == EPI_REDUCE);
+    static constexpr int BK = two ? 16 : 32;     // K' elements per stage
+    static constexpr int KS = BK / KSTEP;        // MMA K steps per stage
+};
+
+template <int S, int MODE>
 struct RowCfg {
-    static constexpr int A_TILE = NP * BK * 2;                 // 8 KB
-    static constexpr int B_TILE = NP * BK * 2;                 // up to 128 rows: 8 KB
+    static constexpr int BK = Pipe<S, MODE>::BK;
+    static constexpr int A_TILE = NP * BK * 2;                 // 4 or 8 KB
+    static constexpr int B_TILE = NP * BK * 2;                 // up to 128 rows
     static constexpr int STAGE_BYTES = S * (A_TILE + B_TILE);
-    static constexpr int STAGES_FIT = (200 * 1024) / STAGE_BYTES;
+    // level-3 hold: [4 column groups][8 float4 slots][128 rows]
+    static constexpr int HOLD_BYTES = Pipe<S, MODE>::two ? 4 * 8 * NP * 16 : 0;
+    // barriers, column tables, reduction partials and row tables (< 17 KB), and 1 KB of
+    // alignment slack
+    static constexpr int TABLES = 19 * 1024;
+    static_assert(2 * 8 * 8 + 3 * 8 + 8 <= 256, "barriers fit the first 256 bytes of the tables");
+    static constexpr int SMEM_MAX = 227 * 1024;
+    static constexpr int STAGES_FIT = (SMEM_MAX - TABLES - HOLD_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
-    // stages, then barriers, column tables, reduction partials and row tables (< 17 KB), and
-    // 1 KB of alignment slack
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 18 * 1024;
-    static_assert(STAGES >= 2, "at least two pipeline stages");
+    static constexpr int SMEM = STAGES * STAGE_BYTES + HOLD_BYTES + TABLES;
+    static_assert(STAGES >= 3 || (!Pipe<S, MODE>::two && STAGES >= 2), "pipeline stages");
+    static_assert(SMEM <= SMEM_MAX, "shared memory");
 };
 
 // A sub-block (rows row0_local .. + 2^lg - 1, which share every digit but the innermost) whose
@@ -466,7 +502,7 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int lg, int64_t r
 // First K' chunk a tile needs. In the reduction (kfrom = 1) the rows are (i, p_1..p_{N-1}) and
 // K = p_N; only non-decreasing tuples are formed, so every valid row of a tile has
 // p_N >= p_{N-1} >= p_{N-2} (its last shared digit) and the chunks below p_{N-2} are zero.
-__device__ __forceinline__ int first_chunk(const RowArgs& a, int lg, int64_t row0_local)
+__device__ __forceinline__ int first_chunk(const RowArgs& a, int lg, int64_t row0_local, int bk)
 {
     if (!a.kfrom || a.N < 3) return 0;
     int d[8];
@@ -475,7 +511,7 @@ __device__ __forceinline__ int first_chunk(const RowArgs& a, int lg, int64_t row
 #pragma unroll
     for (int m = 0; m < 8; ++m)
         if (m == a.N - 3) kmin = d[m];
-    return kmin / 16;   // 16 complex K entries per chunk of 32 K'
+    return kmin / (bk / 2);   // bk / 2 complex K entries per stage of bk K'
 }
 
 // Wait with the same limits and no early exit (draining copies after an error).
@@ -488,68 +524,92 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
     }
 }
 
-// One K' chunk of MMAs: every slice pair (s, u) with s + u < S into its level accumulator, NKS
-// 16-wide K steps (1 when the second half of the chunk is padding). FIRST: the chunk opens the
-// tile, so each level's first MMA overwrites instead of accumulating. The loops unroll into
-// straight-line MMAs with constant descriptor offsets (start address / 16 in the low half).
-template <int S, bool FIRST, int NKS>
-__device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t a_lo, uint32_t b_lo,
-                                            uint32_t idesc)
+// One K' step of MMAs: the slice pairs (s, u), s + u < S, of one pass into their level
+// accumulators. PASS 0: every pair (no hold); PASS 1: the level-3 pairs (s + u >= 3); PASS 2: the
+// pairs of levels 0..2. FIRST: the step opens the pass, so each level's first MMA overwrites
+// instead of accumulating. The loops unroll into straight-line MMAs with constant descriptor
+// offsets (start address / 16 in the low half).
+// NKS: MMA K steps issued from the stage (32-byte K offsets within a 64-byte swizzled row; 1 when
+// the stage's second half is padding). The descriptor's swizzle matches the stage width.
+template <int S, int MODE, int PASS, bool FIRST, int NKS>
+__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_lo, uint32_t b_lo,
+                                            uint32_t b_plane16, uint32_t idesc)
 {
-    using C = RowCfg<S>;
+    using C = RowCfg<S, MODE>;
+    constexpr uint32_t hi = C::BK == 32 ? tc::kSdescSw64Hi : tc::kSdescSw32Hi;
     bool first[4] = {FIRST, FIRST, FIRST, FIRST};
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
         for (int u = 0; u < S - s; ++u) {
             const int L = s + u < 3 ? s + u : 3;
+            if (PASS == 1 && L != 3) continue;
+            if (PASS == 2 && L == 3) continue;
 #pragma unroll
             for (int ks = 0; ks < NKS; ++ks) {
                 const uint32_t ao = a_lo + (uint32_t)((s * C::A_TILE + ks * 32) >> 4);
-                const uint32_t bo = b_lo + (uint32_t)((u * C::B_TILE + ks * 32) >> 4);
-                if (first[L]) tc::mma_bf16_lohi<false>(tmem + L * 128, ao, bo, tc::kSdescSw64Hi, idesc);
-                else tc::mma_bf16_lohi<true>(tmem + L * 128, ao, bo, tc::kSdescSw64Hi, idesc);
+                const uint32_t bo = b_lo + (uint32_t)u * b_plane16 + (uint32_t)(ks * 2);
+                if (first[L]) tc::mma_bf16_lohi<false>(tmem + L * 128, ao, bo, hi, idesc);
+                else tc::mma_bf16_lohi<true>(tmem + L * 128, ao, bo, hi, idesc);
                 first[L] = false;
             }
         }
 }
 
+// Planes a pass reads (level 3 needs every plane; levels 0..2 only planes 0..2).
+template <int S>
+__host__ __device__ constexpr int pass_planes(int pass) { return pass == 2 ? (S < 3 ? S : 3) : S; }
+
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory"); }
 
 // Persistent row GEMM: one CTA per SM walks the tiles blockIdx.x, +gridDim.x, ... Roles:
-//   warp 0 (one lane): TMA producer over a ring of STAGES shared-memory stages that runs across
-//                      tiles, so the next tile's operands stream in during this tile's epilogue;
-//   warp 1 (one lane): MMA issuer; all 512 TMEM columns hold the four level accumulators of one
-//                      128 x bnc-complex tile, so it waits until the epilogue has read them;
-//   warps 2..9       : epilogue (lane quarter = warp % 4, column half = (warp - 2) / 4). Values
+//   warp 0 (one lane): TMA producer over a ring of STAGES shared-memory stages (one 16-wide K'
+//                      step each) that runs across tiles, so the next tile's operands stream in
+//                      during this tile's epilogue;
+//   warp 1 (one lane): MMA issuer. All 512 TMEM columns hold the four level accumulators of one
+//                      128 x bnc-complex tile. With four levels a tile runs in two passes over K:
+//                      first the 15 level-3 slice pairs (S = 6), then the 6 pairs of levels 0..2.
+//                      The epilogue copies level 3 to a shared-memory hold as soon as the tile is
+//                      complete, so the next tile's level-3 pass (most of its MMAs) overlaps the
+//                      rest of this tile's epilogue; only the levels-0..2 pass waits for it;
+//   warps 2..17      : epilogue (lane quarter = warp % 4, column group = (warp - 2) / 4). Values
 //                      needed twice (a column exponent before slicing) are read from TMEM twice
 //                      instead of being staged in shared memory.
+static_assert(sizeof(tfl) == 12 && 6144 + 128 * sizeof(tfl) <= 7680, "table layout");
+static_assert(7680 + 128 * sizeof(RowInfo) + 1024 <= 19 * 1024, "tables and alignment slack");
+
 template <int S, int MODE, bool SUBB>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
-    k_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-           RowArgs args)
+    k_rows(const __grid_constant__ TMaps tmA, const __grid_constant__ TMaps tmB, RowArgs args)
 {
-    using C = RowCfg<S>;
+    using C = RowCfg<S, MODE>;
+    constexpr bool TWO = Pipe<S, MODE>::two;
+    constexpr int BKm = C::BK;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* stage_base = smem;
-    uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+    float4* hold = (float4*)(smem + C::STAGES * C::STAGE_BYTES);   // level-3 hold (S >= 4)
+    // tables at fixed offsets from a 1 KB boundary: barriers and the TMEM slot in the first
+    // 256 bytes (at most 2 x 8 + 3 barriers), then each table 16-byte aligned
+    uint8_t* tables = smem + C::STAGES * C::STAGE_BYTES + C::HOLD_BYTES;
+    uint64_t* full = (uint64_t*)tables;
     uint64_t* empty = full + C::STAGES;
     uint64_t* tfull = empty + C::STAGES;       // MMA -> epilogue: accumulators complete
-    uint64_t* tempty = tfull + 1;              // epilogue -> MMA: accumulators read
-    uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+    uint64_t* tempty = tfull + 1;              // epilogue -> MMA: levels 0..2 (all, no hold) read
+    uint64_t* t3empty = tempty + 1;            // epilogue -> MMA: level 3 copied to the hold
+    uint32_t* tmem_slot = (uint32_t*)(t3empty + 1);
     int* stop = (int*)(tmem_slot + 1);
-    int* colE = (int*)(tmem_slot + 4);         // [4 sub-blocks][64] column exponent keys
-    int* colEb = colE + 4 * 64;                // 64 fixed-matrix column exponents
-    float4* red = (float4*)(colEb + 64);       // [4 lane quarters][64 columns] reduction partials
-    float2* lamf = (float2*)(red + 4 * 64);    // 64 lambda_q in FP32 (exponent estimates)
-    tfl* lamt = (tfl*)(lamf + 64);             // 64 x (Re, Im) lambda_q as exact triple-floats
-    RowInfo* rowinfo = (RowInfo*)(((uintptr_t)(lamt + 128) + 15) & ~(uintptr_t)15);   // [128]
+    int* colE = (int*)(tables + 256);          // [4 sub-blocks][64] column exponent keys
+    int* colEb = (int*)(tables + 1280);        // 64 fixed-matrix column exponents
+    float4* red = (float4*)(tables + 1536);    // [4 lane quarters][64 columns] reduction partials
+    float2* lamf = (float2*)(tables + 5632);   // 64 lambda_q in FP32 (exponent estimates)
+    tfl* lamt = (tfl*)(tables + 6144);         // 64 x (Re, Im) lambda_q as exact triple-floats
+    RowInfo* rowinfo = (RowInfo*)(tables + 7680);   // [128]
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int bnc = args.bnc;
     const int bnr = 2 * bnc;
-    const uint32_t b_bytes_tile = (uint32_t)bnr * BK * 2;
+    const uint32_t b_bytes_tile = (uint32_t)bnr * BKm * 2;
     const int64_t ntiles = args.num_tiles;
     const int ncol = args.ncol_tiles;
     const int lg = SUBB ? args.lg : 7;         // row radix 2^lg (sub-blocks only below 128)
@@ -561,9 +621,12 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         }
         tc::mbar_init(tfull, 1);
         tc::mbar_init(tempty, 1);
+        tc::mbar_init(t3empty, EPI_WARPS);     // one arrival per epilogue warp
         tc::fence_mbar_init();
-        tc::tma_prefetch(&tmA);
-        tc::tma_prefetch(&tmB);
+        tc::tma_prefetch(&tmA.all);
+        tc::tma_prefetch(&tmA.low);
+        tc::tma_prefetch(&tmB.all);
+        tc::tma_prefetch(&tmB.low);
     }
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -576,7 +639,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer
+            // ---------------- TMA producer: per tile one pass over the K' steps with every plane
+            // (no hold), or two: level 3 (every plane), then levels 0..2 (planes 0..2)
             uint32_t it = 0;
             bool alive = true;
             for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
@@ -584,23 +648,23 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const int64_t row0 = tile / ncol * NP;
                 if (tile_skipped(args, lg, row0, ct)) continue;
                 const int bc = ct * bnc;
-                for (int kc = first_chunk(args, lg, row0); kc < args.kch; ++kc, ++it) {
-                    const int st = (int)(it % C::STAGES);
-                    const uint32_t ph = (it / C::STAGES) & 1;
-                    if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) {
-                        alive = false;
-                        break;
-                    }
-                    uint8_t* sA = stage_base + st * C::STAGE_BYTES;
-                    uint8_t* sB = sA + S * C::A_TILE;
-                    tc::mbar_arrive_expect_tx(&full[st], S * (C::A_TILE + b_bytes_tile));
-                    for (int s = 0; s < S; ++s)
-                        tc::tma_load_2d(sA + s * C::A_TILE, &tmA, kc * BK,
-                                        s * args.a_rows + (int)row0, &full[st]);
-                    for (int t = 0; t < S; ++t) {
-                        uint8_t* dst = sB + t * C::B_TILE;
-                        tc::tma_load_2d(dst, &tmB, kc * BK, t * 512 + bc, &full[st]);
-                        tc::tma_load_2d(dst + bnc * BK * 2, &tmB, kc * BK, t * 512 + 256 + bc,
+                const int k0 = first_chunk(args, lg, row0, BKm);
+                for (int pass = TWO ? 1 : 0; pass <= (TWO ? 2 : 0) && alive; ++pass) {
+                    const int np = pass_planes<S>(pass);
+                    for (int kc = k0; kc < args.kch; ++kc, ++it) {
+                        const int st = (int)(it % C::STAGES);
+                        const uint32_t ph = (it / C::STAGES) & 1;
+                        if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) {
+                            alive = false;
+                            break;
+                        }
+                        uint8_t* sA = stage_base + st * C::STAGE_BYTES;
+                        uint8_t* sB = sA + S * C::A_TILE;
+                        tc::mbar_arrive_expect_tx(&full[st], np * (C::A_TILE + b_bytes_tile));
+                        // A: [plane][128 rows][16]; B: [plane][Re rows, Im rows][16]
+                        tc::tma_load_3d(sA, pass == 2 ? &tmA.low : &tmA.all, kc * BKm, (int)row0, 0,
+                                        &full[st]);
+                        tc::tma_load_4d(sB, pass == 2 ? &tmB.low : &tmB.all, kc * BKm, bc, 0, 0,
                                         &full[st]);
                     }
                 }
@@ -614,37 +678,57 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer: slice pairs (s, t), s + t < S, accumulated by level
+            // ---------------- MMA issuer: slice pairs (s, t), s + t < S, accumulated by level.
+            // With the hold, the level-3 pass of a tile starts once the epilogue has copied the
+            // previous tile's level 3 out of TMEM, and the pass of levels 0..2 once the epilogue
+            // has finished the previous tile.
             const uint32_t idesc = tc::idesc_bf16_f32(128, bnr);
+            const uint32_t b16 = b_bytes_tile >> 4;   // B plane stride in 16-byte units
             uint32_t it = 0, t = 0;
             bool alive = true;
             for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
                 const int ct = (int)(tile % ncol);
                 const int64_t row0 = tile / ncol * NP;
                 if (tile_skipped(args, lg, row0, ct)) continue;
-                if (!tc::mbar_wait(tempty, (t & 1) ^ 1, args.err, kErrTimeout)) break;
-                tc::fence_after_sync();
-                const int kc0 = first_chunk(args, lg, row0);
-                for (int kc = kc0; kc < args.kch; ++kc, ++it) {
-                    const int st = (int)(it % C::STAGES);
-                    const uint32_t ph = (it / C::STAGES) & 1;
-                    if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) {
+                const int k0 = first_chunk(args, lg, row0, BKm);
+                for (int pass = TWO ? 1 : 0; pass <= (TWO ? 2 : 0) && alive; ++pass) {
+                    uint64_t* gate = pass == 1 ? t3empty : tempty;
+                    if (!tc::mbar_wait(gate, (t & 1) ^ 1, args.err, kErrTimeout)) {
                         alive = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t aBase = tc::smem_u32(stage_base + st * C::STAGE_BYTES);
-                    const uint32_t a_lo = tc::sdesc_sw64_lo(aBase);
-                    const uint32_t b_lo = tc::sdesc_sw64_lo(aBase + S * C::A_TILE);
-                    const bool half = kc == args.kch - 1 && args.klast == 1;
-                    if (kc == kc0) {
-                        if (half) issue_chunk<S, true, 1>(tmem, a_lo, b_lo, idesc);
-                        else issue_chunk<S, true, 2>(tmem, a_lo, b_lo, idesc);
-                    } else {
-                        if (half) issue_chunk<S, false, 1>(tmem, a_lo, b_lo, idesc);
-                        else issue_chunk<S, false, 2>(tmem, a_lo, b_lo, idesc);
+                    for (int kc = k0; kc < args.kch; ++kc, ++it) {
+                        const int st = (int)(it % C::STAGES);
+                        const uint32_t ph = (it / C::STAGES) & 1;
+                        if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) {
+                            alive = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t aBase = tc::smem_u32(stage_base + st * C::STAGE_BYTES);
+                        const uint32_t a_lo = tc::sdesc_sw64_lo(aBase);
+                        const uint32_t b_lo = tc::sdesc_sw64_lo(aBase + S * C::A_TILE);
+                        if constexpr (TWO) {
+                            if (pass == 1) {
+                                if (kc == k0) issue_kstep<S, MODE, 1, true, 1>(tmem, a_lo, b_lo, b16, idesc);
+                                else issue_kstep<S, MODE, 1, false, 1>(tmem, a_lo, b_lo, b16, idesc);
+                            } else {
+                                if (kc == k0) issue_kstep<S, MODE, 2, true, 1>(tmem, a_lo, b_lo, b16, idesc);
+                                else issue_kstep<S, MODE, 2, false, 1>(tmem, a_lo, b_lo, b16, idesc);
+                            }
+                        } else {
+                            const bool half = kc == args.kch - 1 && args.klast == 1;
+                            if (kc == k0) {
+                                if (half) issue_kstep<S, MODE, 0, true, 1>(tmem, a_lo, b_lo, b16, idesc);
+                                else issue_kstep<S, MODE, 0, true, Pipe<S, MODE>::KS>(tmem, a_lo, b_lo, b16, idesc);
+                            } else {
+                                if (half) issue_kstep<S, MODE, 0, false, 1>(tmem, a_lo, b_lo, b16, idesc);
+                                else issue_kstep<S, MODE, 0, false, Pipe<S, MODE>::KS>(tmem, a_lo, b_lo, b16, idesc);
+                            }
+                        }
+                        tc::mma_commit(&empty[st]);
                     }
-                    tc::mma_commit(&empty[st]);
                 }
                 if (!alive) break;
                 if (!args.stall) tc::mma_commit(tfull);
@@ -797,6 +881,24 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             // warp-uniform (the epilogue's shuffles and TMEM loads are warp-collective)
             const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout));
             tc::fence_after_sync();
+            // this thread's level-3 slots of the hold: Re columns of unit u at slot u, Im at 4 + u
+            float4* held = hold + ((size_t)grp * 8 * NP + rl);
+            if (TWO && ok) {
+                // level 3 out of TMEM first, so that the next tile's level-3 MMAs can start
+                for (int u = 0; u < cols / 4; ++u) {
+                    uint32_t r3[4], i3[4];
+                    tc::tmem_ld4(trow + 3 * 128 + cbeg + 4 * u, r3);
+                    tc::tmem_ld4(trow + bnc + 3 * 128 + cbeg + 4 * u, i3);
+                    tc::tmem_wait_ld();
+                    held[(size_t)u * NP] = make_float4(__uint_as_float(r3[0]), __uint_as_float(r3[1]),
+                                                       __uint_as_float(r3[2]), __uint_as_float(r3[3]));
+                    held[(size_t)(4 + u) * NP] = make_float4(__uint_as_float(i3[0]), __uint_as_float(i3[1]),
+                                                             __uint_as_float(i3[2]), __uint_as_float(i3[3]));
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(t3empty);
+            }
             if (trc && et == 0) trc[1] = global_ns();         // accumulators complete
 
             // h of one element in native FP64 (EPI_SLAB, and EPI_DIVIDE with fp64_quotient):
@@ -887,8 +989,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
                 for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
                     uint32_t rv[4][4], iv[4][4];
-                    load_levels<S>(trow + c4, 128, rv);
-                    load_levels<S>(trow + bnc + c4, 128, iv);
+                    const int u = (c4 - cbeg) / 4;
+                    load_levels<S, TWO>(trow + c4, 128, rv, held + (size_t)u * NP);
+                    load_levels<S, TWO>(trow + bnc + c4, 128, iv, held + (size_t)(4 + u) * NP);
                     tc::tmem_wait_ld();
                     dfl pr[4], pi[4];
 #pragma unroll
@@ -952,8 +1055,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 // pass 2 (or the only pass): outputs
                 for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
                     uint32_t rv[4][4], iv[4][4];
-                    load_levels<S>(trow + c4, 128, rv);
-                    load_levels<S>(trow + bnc + c4, 128, iv);
+                    const int u = (c4 - cbeg) / 4;
+                    load_levels<S, TWO>(trow + c4, 128, rv, held + (size_t)u * NP);
+                    load_levels<S, TWO>(trow + bnc + c4, 128, iv, held + (size_t)(4 + u) * NP);
                     tc::tmem_wait_ld();
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -1266,26 +1370,58 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 2-D BF16 tensor [rows][inner], box {32, box_rows}, 64-byte swizzle.
-static CUtensorMap make_tmap(const void* base, int64_t inner, int64_t rows, int box_rows)
+// BF16 tensor map whose boxes are bk = 16 or 32 elements wide, with the matching 32- or 64-byte
+// swizzle.
+static CUtensorMap encode_map(const void* base, int rank, const cuuint64_t* dims,
+                              const cuuint64_t* strides, const cuuint32_t* box, int bk)
 {
     CUtensorMap m;
-    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
-                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base),
+                             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         fail(NPF_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return m;
 }
 
+// Operands as the callers describe them: data planes [S][rows][inner] and fixed-matrix planes
+// [S][512][inner] (Re rows at 0.., Im rows at 256..), BF16.
+struct DataOp { const void* base; int64_t inner, rows; };
+struct FixedOp { const void* base; int64_t inner; };
+
+// Data operand as a 3-D tensor (inner, rows, plane); box {bk, 128 rows, planes}.
+template <int S>
+static TMaps plane_maps(const DataOp& d, int bk)
+{
+    const cuuint64_t dims[3] = {(cuuint64_t)d.inner, (cuuint64_t)d.rows, (cuuint64_t)S};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.inner * 2, (cuuint64_t)(d.rows * d.inner * 2)};
+    const cuuint32_t box_all[3] = {(cuuint32_t)bk, (cuuint32_t)NP, (cuuint32_t)S};
+    const cuuint32_t box_low[3] = {(cuuint32_t)bk, (cuuint32_t)NP, (cuuint32_t)pass_planes<S>(2)};
+    return {encode_map(d.base, 3, dims, strides, box_all, bk),
+            encode_map(d.base, 3, dims, strides, box_low, bk)};
+}
+
+// Fixed matrix as a 4-D tensor (inner, row within the half, half, plane); box {bk, bnc, 2,
+// planes}, so a plane's tile is its bnc Re rows followed by its bnc Im rows.
+template <int S>
+static TMaps fixed_maps(const FixedOp& f, int bnc, int bk)
+{
+    const cuuint64_t dims[4] = {(cuuint64_t)f.inner, 256, 2, (cuuint64_t)S};
+    const cuuint64_t strides[3] = {(cuuint64_t)f.inner * 2, (cuuint64_t)(256 * f.inner * 2),
+                                   (cuuint64_t)(512 * f.inner * 2)};
+    const cuuint32_t box_all[4] = {(cuuint32_t)bk, (cuuint32_t)bnc, 2, (cuuint32_t)S};
+    const cuuint32_t box_low[4] = {(cuuint32_t)bk, (cuuint32_t)bnc, 2, (cuuint32_t)pass_planes<S>(2)};
+    return {encode_map(f.base, 4, dims, strides, box_all, bk),
+            encode_map(f.base, 4, dims, strides, box_low, bk)};
+}
+
 static int default_slices(const Plan& p)
 {
-    return p.slices ? p.slices : (p.precision == NPF_PREC_FP32 ? 3 : 6);
+    // the FP32 form: 4 slices (32 bits); 3 (FP32's 24) measured 2.0e-5 at n = 80, order 4,
+    // over its 1e-5 bar, after five rounding stages
+    return p.slices ? p.slices : (p.precision == NPF_PREC_FP32 ? 4 : 6);
 }
 
 // Host slicing of x with exponent e into S balanced digits.
@@ -1380,7 +1516,7 @@ template <int S, int MODE, bool SUBB>
 static void smem_attr()
 {
     NPF_CUDA(cudaFuncSetAttribute(k_rows<S, MODE, SUBB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  RowCfg<S>::SMEM));
+                                  RowCfg<S, MODE>::SMEM));
 }
 
 template <int S>
@@ -1571,9 +1707,15 @@ static int sm_count()
 }
 
 template <int S, int MODE>
-static void launch_rows(Plan& p, const char* name, const CUtensorMap& tA, const CUtensorMap& tB,
+// kprime: K' length of the contraction (2 n for complex K, n for real K)
+static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedOp& B, int kprime,
                         RowArgs a)
 {
+    constexpr int bk = RowCfg<S, MODE>::BK;
+    a.kch = (kprime + bk - 1) / bk;            // K' past kprime holds zeros on both sides
+    a.klast = (kprime + KSTEP - 1) / KSTEP - (bk / KSTEP) * (a.kch - 1);
+    const TMaps tA = plane_maps<S>(A, bk);
+    const TMaps tB = fixed_maps<S>(B, a.bnc, bk);
     static const bool tracing = getenv("NPF_TRACE_TILES") != nullptr;
     unsigned long long* dtrace = nullptr;
     if (tracing) {
@@ -1590,10 +1732,10 @@ static void launch_rows(Plan& p, const char* name, const CUtensorMap& tA, const 
         if (grid > 1 && a.ncol_tiles > 1 && grid % 2 == 0) grid -= 1;
         const unsigned g = (unsigned)std::max<int64_t>(grid, 1);
         if constexpr (MODE != EPI_F64T) {
-            if (a.lg < 7) k_rows<S, MODE, true><<<g, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
-            else k_rows<S, MODE, false><<<g, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+            if (a.lg < 7) k_rows<S, MODE, true><<<g, ROW_THREADS, RowCfg<S, MODE>::SMEM, p.stream>>>(tA, tB, a);
+            else k_rows<S, MODE, false><<<g, ROW_THREADS, RowCfg<S, MODE>::SMEM, p.stream>>>(tA, tB, a);
         } else {
-            k_rows<S, MODE, false><<<g, ROW_THREADS, RowCfg<S>::SMEM, p.stream>>>(tA, tB, a);
+            k_rows<S, MODE, false><<<g, ROW_THREADS, RowCfg<S, MODE>::SMEM, p.stream>>>(tA, tB, a);
         }
         NPF_CUDA(cudaGetLastError());
     }
@@ -1674,13 +1816,13 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     // a slab entry whose accumulator is exactly zero is not stored, so the slab starts at zero
     launch_zero(p, d_out, (int64_t)n * n);
 
-    const CUtensorMap tPhi = make_tmap(so.phi, KP, (int64_t)S * 512, bnc);
-    const CUtensorMap tPsiR = make_tmap(so.psir, NP, (int64_t)S * 512, bnc);
-    const CUtensorMap tRed = make_tmap(W ? so.wred : so.red, KP, (int64_t)S * 512, bnc);
-    const CUtensorMap tAT = make_tmap(so.at[N], NP, (int64_t)S * Prows, 128);
-    const CUtensorMap tT0 = make_tmap(T[0], 2 * rad, (int64_t)S * t_rows, 128);
-    const CUtensorMap tT1 = make_tmap(T[1], 2 * rad, (int64_t)S * t_rows, 128);
-    const CUtensorMap* tT[2] = {&tT0, &tT1};
+    const FixedOp tPhi{so.phi, KP};
+    const FixedOp tPsiR{so.psir, NP};
+    const FixedOp tRed{W ? so.wred : so.red, KP};
+    const DataOp tAT{so.at[N], NP, Prows};
+    const DataOp tT0{T[0], 2 * rad, t_rows};
+    const DataOp tT1{T[1], 2 * rad, t_rows};
+    const DataOp* tT[2] = {&tT0, &tT1};
 
     RowArgs base0{};
     base0.n = n;
@@ -1707,8 +1849,6 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     {
         RowArgs a = base0;
         a.a_rows = (int)Prows;
-        a.kch = (n + BK - 1) / BK;   // K = j < n: chunks past n hold zeros only
-        a.klast = (n + 15) / 16 - 2 * (a.kch - 1);
         a.ea = so.at_e[N];
         a.ea_shift = 0;
         a.eb = so.psir_e;
@@ -1719,7 +1859,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         a.npc = n;
         a.out_f64 = Sd;
         a.ld_f64 = Prows;
-        launch_rows<S, EPI_F64T>(p, "split_upper_contraction", tAT, tPsiR, a);
+        launch_rows<S, EPI_F64T>(p, "split_upper_contraction", tAT, tPsiR, n, a);   // K = j < n
     }
     {
         LaunchScope ls(&p.prof, "split_s_records", p.stream);
@@ -1744,8 +1884,6 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         for (int c = 1; c <= N; ++c) {
             RowArgs a = base0;
             a.a_rows = (int)t_rows;
-            a.kch = (2 * n + BK - 1) / BK;   // K' = 2 p + re/im < 2 n
-            a.klast = (2 * n + 15) / 16 - 2 * (a.kch - 1);
             a.ea = c == 1 ? sE + i0 : E[cb];
             a.ea_shift = c == 1 ? lg * (N - 1) : 0;   // c = 1: one exponent per upper index
             a.eb = so.phi_e;
@@ -1762,12 +1900,12 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
             a.out_plane_stride = t_rows * 2 * rad;
             a.out_exp = E[cb ^ 1];
             if (c < N) {
-                launch_rows<S, EPI_SLICE>(p, "split_mode_product", *tT[cb], tPhi, a);
+                launch_rows<S, EPI_SLICE>(p, "split_mode_product", *tT[cb], tPhi, 2 * n, a);
             } else if (slab) {
                 a.out_f64 = d_out;
-                launch_rows<S, EPI_SLAB>(p, "split_mode_divide", *tT[cb], tPhi, a);
+                launch_rows<S, EPI_SLAB>(p, "split_mode_divide", *tT[cb], tPhi, 2 * n, a);
             } else {
-                launch_rows<S, EPI_DIVIDE>(p, "split_mode_divide", *tT[cb], tPhi, a);
+                launch_rows<S, EPI_DIVIDE>(p, "split_mode_divide", *tT[cb], tPhi, 2 * n, a);
             }
             cb ^= 1;
         }
@@ -1775,8 +1913,6 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         // ---- reduction: rows c' = (i, p_1..p_{N-1}), K = p_N, columns k (Psi^T)
         RowArgs a = base0;
         a.a_rows = (int)t_rows;
-        a.kch = (2 * nm + BK - 1) / BK;   // K' = 2 p_N + re/im < 2 nm
-        a.klast = (2 * nm + 15) / 16 - 2 * (a.kch - 1);
         a.ncv = n;                         // columns: states k
         a.kfrom = 1;                       // K = p_N >= the tile's last shared p
         a.ea = E[cb];
@@ -1791,7 +1927,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         a.i0 = i0;
         a.nouter = cur;
         a.out_f64 = d_out;
-        launch_rows<S, EPI_REDUCE>(p, "split_reduce", *tT[cb], tRed, a);
+        launch_rows<S, EPI_REDUCE>(p, "split_reduce", *tT[cb], tRed, 2 * nm, a);   // K = p_N < nm
     }
     if (p.err_override) return;   // the batch reads the shared flag after its graph has run
     int herr = 0;

@@ -94,6 +94,27 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// 3-D and 4-D tiled loads (coordinates innermost first): every slice plane of an operand tile
+// in one copy.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            int w, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---------------------------------------------------------------------------- TMEM
 // Executed by one full warp. Writes the allocated base address to *slot (shared memory).
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
@@ -155,11 +176,15 @@ __device__ __forceinline__ void mma_bf16_lohi(uint32_t d_tmem, uint32_t a_lo, ui
 // BF16 = 64 bytes, 8-row atoms of 512 bytes), as two 32-bit halves: start address >> 4 at bits
 // 0-13, leading byte offset (unused for swizzled K-major, 1) at 16-29; stride byte offset =
 // 512 >> 4 at bits 32-45, descriptor version 1 at 46-47, layout type SWIZZLE_64B = 4 at 61-63.
+// The low half is the same for every swizzle width.
 __device__ __forceinline__ uint32_t sdesc_sw64_lo(uint32_t saddr)
 {
     return ((saddr & 0x3FFFF) >> 4) | (1u << 16);
 }
 constexpr uint32_t kSdescSw64Hi = (512u >> 4) | (1u << 14) | (4u << 29);
+// The same for the 32-byte swizzle (rows of 16 BF16 = 32 bytes, 8-row atoms of 256 bytes): stride
+// byte offset 256 >> 4, layout type SWIZZLE_32B = 6.
+constexpr uint32_t kSdescSw32Hi = (256u >> 4) | (1u << 14) | (6u << 29);
 
 // Arrive once on `bar` when every tcgen05.mma issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar)

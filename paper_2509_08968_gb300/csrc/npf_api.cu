@@ -681,6 +681,25 @@ int npf_compute_prefetch(npf_handle* h, int order, npf_c128* out, int count, con
     });
 }
 
+int npf_finish_terms(npf_handle* h, int count, const npf_c128* terms, npf_c128* out)
+{
+    return guarded([&] {
+        if (!h || !out || count < 0 || (count > 0 && !terms)) npf::fail(NPF_ERR_ARG, "bad argument");
+        Plan& p = h->p;
+        if (p.permuted())
+            npf::fail(NPF_ERR_UNSUPPORTED, "finishing given terms is not available with a mode subset");
+        const int64_t nn = (int64_t)p.n * p.n;
+        npf::launch_zero(p, p.d_sum, nn);
+        for (int t = 0; t < count; ++t) {
+            copy_in(p.d_tmp, terms + (int64_t)t * nn, nn * sizeof(double2), p.stream);
+            npf::launch_add(p, p.d_sum, p.d_tmp, nn);
+        }
+        npf::launch_finish(p, count > 0 ? p.d_sum : nullptr, p.d_npf);
+        NPF_CUDA(cudaMemcpyAsync(out, p.d_npf, nn * sizeof(double2), cudaMemcpyDefault, p.stream));
+        sync(p);
+    });
+}
+
 int npf_interaction(npf_handle* h, int order, double delta, npf_c128* out)
 {
     return guarded([&] {

@@ -4,7 +4,8 @@ Psi_N[i, k] of Eq. 7 sums over the lower indices only, so its rows (the upper in
 independent: disjoint row ranges computed separately (npf_get_term_rows) add up to the whole term.
 This module splits the rows over ranks of a process group (one GPU each; the only exchange is one
 sum of the n x n partial terms, FP64 complex) and over resumable chunks whose partial sums are
-checkpointed to a file after each chunk.
+checkpointed to a file after each chunk; sharded_npf is the whole row-sharded NPF computation
+that the multi-GPU benchmark times.
 """
 from __future__ import annotations
 
@@ -44,6 +45,25 @@ def term_sharded(plan, order, dist, group=None):
     lo, hi = row_ranges(plan.n, world)[rank]
     part = plan.term_rows(order, lo, hi) if hi > lo else np.zeros((plan.n, plan.n), np.complex128)
     return allreduce_sum(part, dist, group)
+
+
+def sharded_npf(plan, orders, dist=None, group=None, out=None):
+    """NPF of the given orders with the upper-index rows of every term split over the ranks of
+    the group: each rank forms its rows of each Psi_N (npf_get_term_rows) into one stacked
+    [orders, n, n] array, one sum over the ranks (FP64 complex: on the GPU with NCCL, on the host
+    with gloo) gives every rank the whole terms, and the library finishes the NPF from them
+    (npf_finish_terms, Algorithm 2 step 20). Without a group the rank forms every row."""
+    import torch
+    rank, world = (dist.get_rank(group), dist.get_world_size(group)) if dist else (0, 1)
+    lo, hi = row_ranges(plan.n, world)[rank]
+    dev = "cuda" if dist is None or dist.get_backend(group) == "nccl" else "cpu"
+    stack = torch.zeros((len(orders), plan.n, plan.n), dtype=torch.complex128, device=dev)
+    for t, N in enumerate(orders):
+        if hi > lo:
+            plan.term_rows(N, lo, hi, out=stack[t])
+    if dist is not None and world > 1:
+        dist.all_reduce(torch.view_as_real(stack), op=dist.ReduceOp.SUM, group=group)
+    return plan.finish_terms(stack, out)
 
 
 class Interrupted(RuntimeError):

@@ -1,7 +1,7 @@
 """Split-BF16 tensor-core path (and its FP32-level form) against the CPU oracle.
 
 Bars from the specification of the path: relative Frobenius error <= 1e-10 for the FP64-emulating
-split form (6 BF16 slices) and <= 1e-5 for the FP32 form (3 slices), for h slabs, Psi_N and NPF.
+split form (6 BF16 slices) and <= 1e-5 for the FP32 form (4 slices), for h slabs, Psi_N and NPF.
 """
 import math
 import os

@@ -23,11 +23,18 @@ class OraclePlan:
                                 self.sysm.lam, p1_block=10)
         self.calls = []
 
-    def term_rows(self, order, lo, hi):
+    def term_rows(self, order, lo, hi, out=None):
         self.calls.append((lo, hi))
-        out = np.zeros_like(self.full)
-        out[lo:hi] = self.full[lo:hi]
-        return out
+        rows = np.zeros_like(self.full)
+        rows[lo:hi] = self.full[lo:hi]
+        if out is not None:
+            out.copy_(__import__("torch").from_numpy(rows))
+            return out
+        return rows
+
+    def finish_terms(self, terms, out=None):
+        S = np.asarray(terms).reshape(-1, self.n, self.n).sum(axis=0)
+        return oracle.npf(self.sysm.U, self.sysm.V, S)
 
 
 def test_row_ranges():
@@ -89,3 +96,37 @@ def test_two_gloo_ranks_split_rows():
     assert got[0][1] == [(0, 5)] and got[1][1] == [(5, 10)]
     for r in range(2):
         np.testing.assert_array_equal(got[r][0], full)   # disjoint rows: the sum is exact
+
+
+def _rank_npf(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    from paper_2509_08968_gb300 import shard as sh
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        plan = OraclePlan()
+        q.put((rank, sh.sharded_npf(plan, (3,), dist), plan.calls))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_sharded_npf():
+    """The row-sharded NPF of the multi-GPU benchmark: each rank forms half the rows, one sum,
+    and every rank's NPF equals the single-process one."""
+    pytest.importorskip("torch")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_npf, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict((r, (t, c)) for r, t, c in (q.get(timeout=120) for _ in range(2)))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    plan = OraclePlan()
+    ref = oracle.npf(plan.sysm.U, plan.sysm.V, plan.full)
+    assert got[0][1] == [(0, 5)] and got[1][1] == [(5, 10)]
+    for r in range(2):
+        np.testing.assert_array_equal(got[r][0], ref)
