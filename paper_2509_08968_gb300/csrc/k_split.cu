@@ -108,6 +108,13 @@ __device__ __forceinline__ float byte_to_digit(uint32_t u, int s)
     return fmaf(__uint_as_float(0x4B000000u | u), sc, -8388736.0f * sc);
 }
 
+// The float 2^23 + u for the byte u at position k (0..3) of x: one byte permute places the byte
+// under the exponent bits 0x4B (bytes 1 and 2 zero).
+__device__ __forceinline__ float byte_float(uint32_t x, int k)
+{
+    return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7440u | (uint32_t)k));
+}
+
 template <int S>
 __device__ __forceinline__ void digit_pairs(long long Wr, long long Wi, uint32_t (&out)[S])
 {
@@ -126,10 +133,10 @@ __device__ __forceinline__ void digit_pairs(long long Wr, long long Wi, uint32_t
             fr = byte_to_digit((uint32_t)(tr + 128), 0);
             fi = byte_to_digit((uint32_t)(ti + 128), 0);
         } else {
-            const uint32_t br = k < 4 ? (rlo >> (8 * k)) & 255u : (rhi >> (8 * (k - 4))) & 255u;
-            const uint32_t bi = k < 4 ? (ilo >> (8 * k)) & 255u : (ihi >> (8 * (k - 4))) & 255u;
-            fr = byte_to_digit(br, s);
-            fi = byte_to_digit(bi, s);
+            // (2^23 + u) 2^(-8s) - (2^23 + 128) 2^(-8s) = (u - 128) 2^(-8s), exact
+            const float sc = pow2f(-8 * s);
+            fr = fmaf(k < 4 ? byte_float(rlo, k) : byte_float(rhi, k - 4), sc, -8388736.0f * sc);
+            fi = fmaf(k < 4 ? byte_float(ilo, k) : byte_float(ihi, k - 4), sc, -8388736.0f * sc);
         }
         // both are exact BF16 values: their upper halves are the BF16 bits (Re low, Im high)
         out[s] = __byte_perm(__float_as_uint(fr), __float_as_uint(fi), 0x7632);
@@ -221,13 +228,22 @@ __device__ __forceinline__ long long df_round_i64(dfl x)
 
 // Per-row values of the quotient epilogues.
 struct RowInfo {
-    double2 sigma;        // sum of the row's p eigenvalues minus lambda_i
+    double2 sigma;        // sum of the row's p eigenvalues minus lambda_i (lambda_{p_N} alone
+                          // when the per-column sums carry the rest)
     double mult_base;     // N! / prod(run lengths)!
     tfl sr, si;           // sigma as exact triple-floats
     dfl f_row, f_first;   // mult_base / N! (and with the first run one longer) as double-floats
     int run1;
-    int pad;
+    float fmb;            // mult_base / N! in FP32 (exponent estimates)
 };
+
+// 1 / d for a small positive integer d as a double-float (relative error ~2^-46), without FP64.
+__device__ __forceinline__ dfl rcp_small(int d)
+{
+    const float x = (float)d;                        // exact
+    const float hi = __frcp_rn(x);
+    return {hi, fmaf(-hi, x, 1.0f) * hi};            // the residual 1 - hi x is exact
+}
 
 // Recombined accumulator of one output element: V (units 2^-30 of the L0 integer grid). The
 // integer parts are read off float bit patterns after adding 1.5 * 2^(23 + j): the sum lands in a
@@ -402,6 +418,8 @@ struct RowArgs {
                          // output row is also written for the swapped pair of shared a's
                          // (orders <= 4 have at most two shared a's)
     int64_t R;           // rows per outer index (output layout [outer][q][r])
+    int lgR;             // log2(R) when R is a power of two (digit rows), else -1
+    int lgncol;          // log2(ncol_tiles)
     int npc;             // extent of the new index in the output layout
     int lg;              // log2 of the row radix (digits, and the next operand's K extent)
     int n;               // states (range of the a digits and of the reduction's columns k)
@@ -417,6 +435,7 @@ struct RowArgs {
     const double2* lam;
     const double2* V;        // psi_{p k} at p*n + k
     const float4* psi_df;    // the same as double-float
+    const float* lam_t;      // lambda_p as exact triple-floats [n][Re a, b, c, Im a, b, c]
     int i0;
     double invfact, eps;
     int divide;
@@ -446,6 +465,9 @@ struct Pipe {
     static constexpr bool two = Lev<S>::N == 4 && (MODE == EPI_DIVIDE || MODE == EPI_REDUCE);
     static constexpr int BK = two ? 16 : 32;     // K' elements per stage
     static constexpr int KS = BK / KSTEP;        // MMA K steps per stage
+    // K steps per stage of the second pass, which reads planes 0..2 only: as many as the
+    // stage's S plane slots hold, so the ring keeps as many bytes in flight as in the first pass
+    static constexpr int P2 = two ? S / 3 : 1;
 };
 
 template <int S, int MODE>
@@ -468,12 +490,23 @@ struct RowCfg {
     static_assert(SMEM <= SMEM_MAX, "shared memory");
 };
 
+// Row index within / across the outer index (shifts for the power-of-two digit layouts: 64-bit
+// divisions by a runtime divisor cost ~70 instructions, and every role decodes every tile).
+__device__ __forceinline__ int64_t row_in_outer(const RowArgs& a, int64_t o)
+{
+    return a.lgR >= 0 ? (o & ((1ll << a.lgR) - 1)) : o % a.R;
+}
+__device__ __forceinline__ int64_t outer_of(const RowArgs& a, int64_t o)
+{
+    return a.lgR >= 0 ? (o >> a.lgR) : o / a.R;
+}
+
 // A sub-block (rows row0_local .. + 2^lg - 1, which share every digit but the innermost) whose
 // rows are all padding, or that the sorted-tuple rules exclude.
 __device__ __forceinline__ bool block_skipped(const RowArgs& a, int lg, int64_t row0_local, int ct)
 {
     int d[8];
-    row_digits(row0_local % a.R, a.N - 1, lg, d);
+    row_digits(row_in_outer(a, row0_local), a.N - 1, lg, d);
     const int nd = a.N - 1;
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
@@ -506,7 +539,7 @@ __device__ __forceinline__ int first_chunk(const RowArgs& a, int lg, int64_t row
 {
     if (!a.kfrom || a.N < 3) return 0;
     int d[8];
-    row_digits(row0_local % a.R, a.N - 1, lg, d);   // sub-block 0 has the smallest p_{N-2}
+    row_digits(row_in_outer(a, row0_local), a.N - 1, lg, d);   // sub-block 0: smallest p_{N-2}
     int kmin = 0;
 #pragma unroll
     for (int m = 0; m < 8; ++m)
@@ -644,14 +677,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             uint32_t it = 0;
             bool alive = true;
             for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
-                const int ct = (int)(tile % ncol);
-                const int64_t row0 = tile / ncol * NP;
+                const int ct = (int)(tile & (ncol - 1));
+                const int64_t row0 = (tile >> args.lgncol) * NP;
                 if (tile_skipped(args, lg, row0, ct)) continue;
                 const int bc = ct * bnc;
                 const int k0 = first_chunk(args, lg, row0, BKm);
                 for (int pass = TWO ? 1 : 0; pass <= (TWO ? 2 : 0) && alive; ++pass) {
                     const int np = pass_planes<S>(pass);
-                    for (int kc = k0; kc < args.kch; ++kc, ++it) {
+                    const int kstride = pass == 2 ? Pipe<S, MODE>::P2 : 1;
+                    for (int kc = k0; kc < args.kch; kc += kstride, ++it) {
                         const int st = (int)(it % C::STAGES);
                         const uint32_t ph = (it / C::STAGES) & 1;
                         if (!tc::mbar_wait(&empty[st], ph ^ 1, args.err, kErrTimeout)) {
@@ -660,12 +694,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         }
                         uint8_t* sA = stage_base + st * C::STAGE_BYTES;
                         uint8_t* sB = sA + S * C::A_TILE;
-                        tc::mbar_arrive_expect_tx(&full[st], np * (C::A_TILE + b_bytes_tile));
-                        // A: [plane][128 rows][16]; B: [plane][Re rows, Im rows][16]
-                        tc::tma_load_3d(sA, pass == 2 ? &tmA.low : &tmA.all, kc * BKm, (int)row0, 0,
-                                        &full[st]);
-                        tc::tma_load_4d(sB, pass == 2 ? &tmB.low : &tmB.all, kc * BKm, bc, 0, 0,
-                                        &full[st]);
+                        const int nks = min(kstride, args.kch - kc);   // K steps in this stage
+                        tc::mbar_arrive_expect_tx(&full[st], nks * np * (C::A_TILE + b_bytes_tile));
+                        // A: [step][plane][128 rows][16]; B: [step][plane][Re rows, Im rows][16]
+                        for (int j = 0; j < nks; ++j) {
+                            tc::tma_load_3d(sA + j * np * C::A_TILE, pass == 2 ? &tmA.low : &tmA.all,
+                                            (kc + j) * BKm, (int)row0, 0, &full[st]);
+                            tc::tma_load_4d(sB + j * np * b_bytes_tile, pass == 2 ? &tmB.low : &tmB.all,
+                                            (kc + j) * BKm, bc, 0, 0, &full[st]);
+                        }
                     }
                 }
             }
@@ -687,8 +724,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             uint32_t it = 0, t = 0;
             bool alive = true;
             for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
-                const int ct = (int)(tile % ncol);
-                const int64_t row0 = tile / ncol * NP;
+                const int ct = (int)(tile & (ncol - 1));
+                const int64_t row0 = (tile >> args.lgncol) * NP;
                 if (tile_skipped(args, lg, row0, ct)) continue;
                 const int k0 = first_chunk(args, lg, row0, BKm);
                 for (int pass = TWO ? 1 : 0; pass <= (TWO ? 2 : 0) && alive; ++pass) {
@@ -698,7 +735,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         break;
                     }
                     tc::fence_after_sync();
-                    for (int kc = k0; kc < args.kch; ++kc, ++it) {
+                    const int kstride = pass == 2 ? Pipe<S, MODE>::P2 : 1;
+                    for (int kc = k0; kc < args.kch; kc += kstride, ++it) {
                         const int st = (int)(it % C::STAGES);
                         const uint32_t ph = (it / C::STAGES) & 1;
                         if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) {
@@ -714,8 +752,14 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                                 if (kc == k0) issue_kstep<S, MODE, 1, true, 1>(tmem, a_lo, b_lo, b16, idesc);
                                 else issue_kstep<S, MODE, 1, false, 1>(tmem, a_lo, b_lo, b16, idesc);
                             } else {
-                                if (kc == k0) issue_kstep<S, MODE, 2, true, 1>(tmem, a_lo, b_lo, b16, idesc);
-                                else issue_kstep<S, MODE, 2, false, 1>(tmem, a_lo, b_lo, b16, idesc);
+                                constexpr int np2 = pass_planes<S>(2);
+                                const int nks = min(kstride, args.kch - kc);
+                                for (int j = 0; j < nks; ++j) {
+                                    const uint32_t aj = a_lo + (uint32_t)(j * np2 * C::A_TILE / 16);
+                                    const uint32_t bj = b_lo + (uint32_t)(j * np2) * b16;
+                                    if (kc == k0 && j == 0) issue_kstep<S, MODE, 2, true, 1>(tmem, aj, bj, b16, idesc);
+                                    else issue_kstep<S, MODE, 2, false, 1>(tmem, aj, bj, b16, idesc);
+                                }
                             }
                         } else {
                             const bool half = kc == args.kch - 1 && args.klast == 1;
@@ -746,17 +790,18 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         const int N = args.N, n = args.n;
         uint32_t t = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int ct = (int)(tile % ncol);
-            const int64_t row0 = tile / ncol * NP;
+            const int ct = (int)(tile & (ncol - 1));
+            const int64_t row0 = (tile >> args.lgncol) * NP;
             if (tile_skipped(args, lg, row0, ct)) continue;
             unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
             const int qbase = ct * bnc;
             const int64_t o = row0 + rl;                      // local row of the launch
             const int ea = args.ea[o >> args.ea_shift];
-            const int64_t outer = o / args.R;
-            const int64_t rr = o % args.R;
+            const int64_t outer = outer_of(args, o);
+            const int64_t rr = row_in_outer(args, o);
             const int64_t rblk = rr >> lg;                    // the next operand's row within [outer][q]
             const int64_t rperq = args.R >> lg;
+            const int64_t row_base = outer * args.npc * rperq + rblk;   // + qc rperq: next row
             const int kpos = rl & ((1 << lg) - 1);            // ... and the K position in it
             const int sb = rl >> lg;                          // sub-block of the tile (warp-uniform)
             // columns of this tile that any row uses: below the modes in use and, with the
@@ -770,7 +815,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 int pmax = 0;
                 for (int b = 0; b < (NP >> lg); ++b) {
                     int d0[8];
-                    row_digits((row0 + ((int64_t)b << lg)) % args.R, N - 1, lg, d0);
+                    row_digits(row_in_outer(args, row0 + ((int64_t)b << lg)), N - 1, lg, d0);
                     pmax = max(pmax, d0[0]);
                 }
                 vcols = min(vcols, pmax - qbase + 1);
@@ -817,19 +862,72 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             // per-tile tables: column exponents, the fixed matrix's column exponents, lambda_q
             // (FP32 and as exact triple-floats); per row (one thread of each row): sigma of the
             // row p's minus lambda_i, the multiplicity base and the first run length
+            // Divide tiles without sub-blocks share every row digit but the innermost (p_N), so
+            // D = sigma_row + lambda_q = (shared p's lambdas - lambda_i + lambda_q) + lambda_{p_N}:
+            // the bracket once per column in FP64, lambda_{p_N} per row from a triple-float
+            // table, the multiplicities from integer run lengths (FP64 runs at a small fraction
+            // of the FP32 rate, and the per-row sums and divisions made this set-up longer than
+            // the tile's epilogue).
+            if (trc && et == 0) trc[5] = global_ns();         // set-up starts
+            // The three set-up jobs run on three warp groups at once: the column tables (warps of
+            // group 0), the column sums and eigenvalues (group 1), the row table (group 2).
+            const bool fastdiv = MODE == EPI_DIVIDE && !SUBB && !args.fp64_quotient;
             if (et < 64) {
 #pragma unroll
                 for (int b = 0; b < 4; ++b) colE[64 * b + et] = 0;
                 colEb[et] = args.eb[qbase + et];
-                if (MODE == EPI_DIVIDE) {
-                    const int q = qbase + et;
-                    const double2 lq = q < args.ncv ? args.lam[q] : make_double2(0.0, 0.0);
-                    lamf[et] = make_float2((float)lq.x, (float)lq.y);
-                    lamt[2 * et] = to_tfl(lq.x);
-                    lamt[2 * et + 1] = to_tfl(lq.y);
+            }
+            if (MODE == EPI_DIVIDE && et >= 128 && et < 192) {
+                {
+                    const int c = et - 128;
+                    const int q = qbase + c;
+                    double2 lq = q < args.ncv ? args.lam[q] : make_double2(0.0, 0.0);
+                    if (fastdiv) {
+                        lq = csub(lq, args.lam[args.i0 + (int)outer]);
+#pragma unroll
+                        for (int m = 0; m < 6; ++m)
+                            if (m < N - 2) lq = cadd(lq, args.lam[dg[m]]);
+                    }
+                    lamf[c] = make_float2((float)lq.x, (float)lq.y);
+                    lamt[2 * c] = to_tfl(lq.x);
+                    lamt[2 * c + 1] = to_tfl(lq.y);
                 }
             }
-            if ((MODE == EPI_DIVIDE || MODE == EPI_SLAB) && grp == 0) {
+            if (fastdiv && grp == 2) {
+                int den = 1, run = 1, r1 = 1;
+                bool first_run = true;
+                int pN = 0;
+#pragma unroll
+                for (int m = 1; m < 8; ++m) {
+                    if (m == N - 1) pN = dg[m - 1];
+                    if (m > N - 1) break;
+                    if (m < N - 1 && dg[m] == dg[m - 1]) {
+                        ++run;
+                    } else {
+                        if (first_run) r1 = run;
+                        first_run = false;
+                        for (int u = 2; u <= run; ++u) den *= u;
+                        run = 1;
+                    }
+                }
+                RowInfo ri;
+                ri.mult_base = 0.0;   // not read on this path
+                ri.run1 = r1;
+                ri.fmb = 1.0f / (float)den;
+                ri.f_row = rcp_small(den);
+                ri.f_first = rcp_small(den * (r1 + 1));
+                if (row_ok) {
+                    const float* lt = args.lam_t + 6 * pN;
+                    ri.sr = {lt[0], lt[1], lt[2]};
+                    ri.si = {lt[3], lt[4], lt[5]};
+                    ri.sigma = args.lam[pN];
+                } else {
+                    ri.sr = {0.f, 0.f, 0.f};
+                    ri.si = {0.f, 0.f, 0.f};
+                    ri.sigma = make_double2(0.0, 0.0);
+                }
+                rowinfo[rl] = ri;
+            } else if ((MODE == EPI_DIVIDE || MODE == EPI_SLAB) && grp == 2) {
                 double2 sg = make_double2(0, 0);
                 const int np_row = args.rp;
                 if (row_ok) {
@@ -864,20 +962,27 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const double f = args.invfact * ri.mult_base;
                 ri.f_row = to_dfl(f);
                 ri.f_first = to_dfl(f / (r1 + 1));
+                ri.fmb = (float)f;
                 rowinfo[rl] = ri;
             }
-            if (et == 0) *stop = *(volatile int*)args.err;
+            // another role's error is picked up every 8 tiles (the waits see it at once)
+            if (et == 0 && (t & 7) == 0) *stop = *(volatile int*)args.err;
             epi_sync();
             if (*stop) break;                                // uniform over the epilogue warps
             double2 sigma = make_double2(0, 0);
             double mult_base = 1.0;
             int run1 = 1;
+            float fmb = 1.0f;
             if (MODE == EPI_DIVIDE || MODE == EPI_SLAB) {
                 sigma = rowinfo[rl].sigma;
                 mult_base = rowinfo[rl].mult_base;
                 run1 = rowinfo[rl].run1;
+                fmb = rowinfo[rl].fmb;
             }
-            if (trc && et == 0) trc[0] = global_ns();
+            if (trc && et == 0) {
+                trc[0] = global_ns();
+                trc[4] = blockIdx.x + 1;
+            }
             // warp-uniform (the epilogue's shuffles and TMEM loads are warp-collective)
             const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout));
             tc::fence_after_sync();
@@ -928,7 +1033,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 // FP32 upper bound of |h| = |V| 2^(ea+eb-VEXP) f / |D| with a lower bound of the
                 // clamped |D| (FP32 error of sigma + lambda_q bounded by 4 ulp of its terms).
                 const float2 sf = make_float2((float)sigma.x, (float)sigma.y);
-                const float fmb = (float)(args.invfact * mult_base);
+
                 if (ok) {
                     constexpr float deep = deep_level_bound(S);
                     for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
@@ -1098,7 +1203,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         }
                         if (args.colmask && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
                         if (no_write) continue;
-                        const int64_t rowp = (outer * args.npc + qc) * rperq + rblk;
+                        const int64_t rowp = row_base + (int64_t)qc * rperq;
                         const int key = colE[64 * sb + cl];
                         const int E = key ? key - 8192 : EXP_NONE;
                         uint32_t w[S];
@@ -1174,12 +1279,12 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         // recover (i, p_1..p_{N-2}) from the sub-block's first row
                         const int64_t rb = row0 + ((int64_t)b << lg);
                         int d0[8];
-                        row_digits(rb % args.R, N - 1, lg, d0);
+                        row_digits(row_in_outer(args, rb), N - 1, lg, d0);
                         double2 wgt = make_double2(1.0, 0.0);
 #pragma unroll
                         for (int m = 0; m < 6; ++m)
                             if (m < N - 2) wgt = cmul(wgt, args.V[(int64_t)d0[m] * n + qc]);
-                        const int i = args.i0 + (int)(rb / args.R);
+                        const int i = args.i0 + (int)outer_of(args, rb);
                         const double2 v = cmul(make_double2(df_to_d(ar), df_to_d(ai)), wgt);
                         atomicAdd(&args.out_f64[(int64_t)i * n + qc].x, -v.x);
                         atomicAdd(&args.out_f64[(int64_t)i * n + qc].y, -v.y);
@@ -1341,6 +1446,7 @@ struct SplitOperand {
     __nv_bfloat16* psir = nullptr;  int* psir_e = nullptr;   // Psi, real K (j), columns i
     __nv_bfloat16* red = nullptr;   int* red_e = nullptr;    // Psi^T rows k, complex K (p)
     float4* psi_df = nullptr;
+    float* lam_t = nullptr;         // lambda_p as exact triple-floats [n][Re a, b, c, Im a, b, c]
     // per order: A^T digit planes (rows Q, K' = j) and row exponents
     __nv_bfloat16* at[kMaxOrder + 1] = {};
     int* at_e[kMaxOrder + 1] = {};
@@ -1504,6 +1610,7 @@ void split_release(Plan& p)
     cudaFree(so->psir); cudaFree(so->psir_e);
     cudaFree(so->red); cudaFree(so->red_e);
     cudaFree(so->psi_df);
+    cudaFree(so->lam_t);
     for (int N = 0; N <= kMaxOrder; ++N) { cudaFree(so->at[N]); cudaFree(so->at_e[N]); }
     cudaFree(so->wred); cudaFree(so->wred_e); cudaFree(so->w_df);
     for (int N = 0; N <= kMaxOrder; ++N) cudaFree(so->prefixes[N]);
@@ -1574,6 +1681,21 @@ static void fill_fixed(Plan& p, SplitOperand* so)
         pdf[t] = make_float4(rh, (float)(V[t].x - rh), ih, (float)(V[t].y - ih));
     }
     put(so->psi_df, pdf);
+    // eigenvalues as exact triple-floats (24 + 24 + 5 significant bits of a double)
+    std::vector<double2> lam(n);
+    NPF_CUDA(cudaMemcpy(lam.data(), p.d_lam, n * sizeof(double2), cudaMemcpyDeviceToHost));
+    std::vector<float> lt((size_t)6 * n);
+    auto split3 = [](double x, float* o) {
+        o[0] = (float)x;
+        const double r = x - (double)o[0];
+        o[1] = (float)r;
+        o[2] = (float)(r - (double)o[1]);
+    };
+    for (int q = 0; q < n; ++q) {
+        split3(lam[q].x, &lt[6 * q]);
+        split3(lam[q].y, &lt[6 * q + 3]);
+    }
+    put(so->lam_t, lt);
 }
 
 static SplitOperand& prepare(Plan& p)
@@ -1672,9 +1794,10 @@ void split_prepare_tensor(Plan& p, int N)
 // phase times (%globaltimer) and prints the median phase durations to stderr.
 static void trace_report(const char* name, const std::vector<unsigned long long>& t, int64_t tiles)
 {
-    std::vector<double> d[3];
+    std::vector<double> d[5];
     unsigned long long t0 = ~0ull, t1 = 0;
     int64_t ran = 0;
+    std::map<unsigned long long, std::vector<std::pair<unsigned long long, unsigned long long>>> cta;
     for (int64_t k = 0; k < tiles; ++k) {
         const unsigned long long* r = &t[k * 6];
         if (!r[0] || !r[3]) continue;
@@ -1684,15 +1807,33 @@ static void trace_report(const char* name, const std::vector<unsigned long long>
         d[0].push_back((double)(r[1] - r[0]));                   // epilogue waiting for the MMA
         d[1].push_back(r[2] ? (double)(r[2] - r[1]) : 0.0);      // column-exponent pass
         d[2].push_back((double)(r[3] - (r[2] ? r[2] : r[1])));   // output pass
+        cta[r[4]].push_back({r[0], r[3]});
+        if (r[5]) d[4].push_back((double)(r[0] - r[5]));        // the tile's set-up
+    }
+    // between a CTA's tiles: skipped tiles, the per-tile tables and the error-flag read
+    double busy = 0.0;
+    for (auto& kv : cta) {
+        auto& v = kv.second;
+        std::sort(v.begin(), v.end());
+        for (size_t j = 0; j + 1 < v.size(); ++j) d[3].push_back((double)(v[j + 1].first - v[j].second));
+        if (!v.empty()) busy = std::max(busy, (double)(v.back().second - v.front().first));
     }
     auto med = [](std::vector<double>& v) {
         if (v.empty()) return 0.0;
         std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
         return v[v.size() / 2] * 1e-3;
     };
-    fprintf(stderr, "[trace] %s tiles %lld ran %lld span %.1f us | median us: wait-mma %.2f "
-            "pass1 %.2f pass2 %.2f\n", name, (long long)tiles, (long long)ran,
-            (t1 > t0 ? (t1 - t0) : 0) * 1e-3, med(d[0]), med(d[1]), med(d[2]));
+    auto mean = [](const std::vector<double>& v) {
+        double a = 0.0;
+        for (double x : v) a += x;
+        return v.empty() ? 0.0 : a / v.size() * 1e-3;
+    };
+    fprintf(stderr, "[trace] %s tiles %lld ran %lld span %.1f us (longest CTA %.1f) | median/mean "
+            "us: wait-mma %.2f/%.2f pass1 %.2f/%.2f pass2 %.2f/%.2f between %.2f/%.2f (set-up "
+            "%.2f/%.2f)\n", name,
+            (long long)tiles, (long long)ran, (t1 > t0 ? (t1 - t0) : 0) * 1e-3, busy * 1e-3,
+            med(d[0]), mean(d[0]), med(d[1]), mean(d[1]), med(d[2]), mean(d[2]), med(d[3]),
+            mean(d[3]), med(d[4]), mean(d[4]));
 }
 
 static int sm_count()
@@ -1713,6 +1854,9 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
 {
     constexpr int bk = RowCfg<S, MODE>::BK;
     a.kch = (kprime + bk - 1) / bk;            // K' past kprime holds zeros on both sides
+    a.lgR = (a.R > 0 && (a.R & (a.R - 1)) == 0) ? __builtin_ctzll((unsigned long long)a.R) : -1;
+    a.lgncol = __builtin_ctz((unsigned)a.ncol_tiles);
+    if ((a.ncol_tiles & (a.ncol_tiles - 1)) != 0) fail(NPF_ERR_ARG, "column tiles must be a power of two");
     a.klast = (kprime + KSTEP - 1) / KSTEP - (bk / KSTEP) * (a.kch - 1);
     const TMaps tA = plane_maps<S>(A, bk);
     const TMaps tB = fixed_maps<S>(B, a.bnc, bk);
@@ -1831,6 +1975,7 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     base0.N = N;
     base0.V = W ? W : p.d_V;              // reduction weights (the prefix factors)
     base0.psi_df = W ? so.w_df : so.psi_df;
+    base0.lam_t = so.lam_t;
     base0.lam = p.d_lam;
     base0.invfact = 1.0 / factorial(N);
     base0.eps = p.eps;

@@ -12,7 +12,10 @@ Run from the repository root:  python tests/golden/make_golden.py [order4 | radi
     n80_seed1_order4.npz  : Psi_4 of the n = 80 system (seed 1), ~25 min on 8 cores.
   n120order4:
     n120_seed0_order4.npz : Psi_4 of the n = 120 system (seed 0), the full order-4 term of the
-                            benchmarked system, ~3-4 h on 8 cores.
+                            benchmarked system, ~6 h on 8 cores.
+  npf34 (after the two n = 120 terms exist):
+    n120_seed0_npf34.npz  : NPF of the n = 120 system with its order-3 and order-4 terms
+                            (Algorithm 2 step 20), the output of the benchmarked call.
 """
 import os
 import sys
@@ -90,3 +93,17 @@ if __name__ == "__main__" and "radix128" in sys.argv:
 
 if __name__ == "__main__" and "n120order4" in sys.argv:
     n120_order4()
+
+
+def npf34():
+    """NPF (Alg. 2 step 20) of the n = 120 system from the stored Psi_3 and Psi_4."""
+    sysm = S.config_n120(0, orders=())
+    psi3 = np.load(os.path.join(HERE, "n120_seed0_order3.npz"))["psi3"]
+    psi4 = np.load(os.path.join(HERE, "n120_seed0_order4.npz"))["psi4"]
+    npf = oracle.npf(sysm.U, sysm.V, psi3 + psi4)
+    np.savez_compressed(os.path.join(HERE, "n120_seed0_npf34.npz"), npf=npf)
+    print(f"n120 NPF of orders 3+4: |NPF|_F = {np.linalg.norm(npf):.6e}", flush=True)
+
+
+if __name__ == "__main__" and "npf34" in sys.argv:
+    npf34()
