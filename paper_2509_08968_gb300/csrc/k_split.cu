@@ -420,6 +420,15 @@ struct RowArgs {
     int64_t R;           // rows per outer index (output layout [outer][q][r])
     int lgR;             // log2(R) when R is a power of two (digit rows), else -1
     int lgncol;          // log2(ncol_tiles)
+    // compact reduction rows (order >= 3, row radix 128): the reduction's operand rows are the
+    // sorted tuples (i, p_1 <= .. <= p_{N-1}) in lexicographic rank, RT rows per upper index (Q of
+    // them valid, then padding to whole tiles). EPI_DIVIDE writes them, EPI_REDUCE reads them.
+    int cmp;
+    int64_t Q, RT;
+    const int64_t* cnt;      // tuple-rank table: cnt[r*(n+1) + v] = non-decreasing r-tuples in [v, n)
+    const uint32_t* tuples;  // the sorted (N-1)-tuples in rank order, 8 bits per index
+    const float4* wpre;      // prod_{m <= N-2} W[p_m][k] per sorted (N-2)-tuple (rank) and k,
+                             // as double-float complex
     int npc;             // extent of the new index in the output layout
     int lg;              // log2 of the row radix (digits, and the next operand's K extent)
     int n;               // states (range of the a digits and of the reduction's columns k)
@@ -490,6 +499,9 @@ struct RowCfg {
     static_assert(SMEM <= SMEM_MAX, "shared memory");
 };
 
+// Compact reduction input: the reduction launch (kfrom) with compact rows.
+#define MODE_IS_COMPACT_INPUT(a) ((a).cmp && (a).kfrom)
+
 // Row index within / across the outer index (shifts for the power-of-two digit layouts: 64-bit
 // divisions by a runtime divisor cost ~70 instructions, and every role decodes every tile).
 __device__ __forceinline__ int64_t row_in_outer(const RowArgs& a, int64_t o)
@@ -526,6 +538,7 @@ __device__ __forceinline__ bool block_skipped(const RowArgs& a, int lg, int64_t 
 __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int lg, int64_t row0_local, int ct)
 {
     if (ct * a.bnc >= a.ncv) return true;                  // every column is padding
+    if (MODE_IS_COMPACT_INPUT(a)) return row_in_outer(a, row0_local) >= a.Q;   // padding rows
     if (!a.digits) return false;
     for (int sb = 0; sb < (NP >> lg); ++sb)
         if (!block_skipped(a, lg, row0_local + ((int64_t)sb << lg), ct)) return false;
@@ -538,6 +551,11 @@ __device__ __forceinline__ bool tile_skipped(const RowArgs& a, int lg, int64_t r
 __device__ __forceinline__ int first_chunk(const RowArgs& a, int lg, int64_t row0_local, int bk)
 {
     if (!a.kfrom || a.N < 3) return 0;
+    if (MODE_IS_COMPACT_INPUT(a)) {
+        // rank order: p_1 never decreases along the rows, and every K = p_N >= p_1
+        const int r = (int)row_in_outer(a, row0_local);
+        return (int)(a.tuples[r] & 255u) / (bk / 2);
+    }
     int d[8];
     row_digits(row_in_outer(a, row0_local), a.N - 1, lg, d);   // sub-block 0: smallest p_{N-2}
     int kmin = 0;
@@ -891,7 +909,39 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     lamf[c] = make_float2((float)lq.x, (float)lq.y);
                     lamt[2 * c] = to_tfl(lq.x);
                     lamt[2 * c + 1] = to_tfl(lq.y);
+                    if (args.cmp) {
+                        // compact reduction row of (p_1 = q, the tile's shared p's)
+                        int tup[8];
+                        tup[0] = q;
+                        bool srt = q < args.ncv && q <= dg[0];
+#pragma unroll
+                        for (int m = 0; m < 6; ++m)
+                            if (m < N - 2) tup[m + 1] = dg[m];
+                        ((int*)red)[c] = srt ? (int)tuple_rank(tup, N - 1, args.cnt, n) : -1;
+                    }
                 }
+            }
+            if (MODE == EPI_REDUCE && args.cmp && grp == 2) {
+                // compact rows: the row's tuple, its last index p_{N-1} and the rank of its prefix
+                const int64_t r = rr;
+                int v = -1;
+                if (r < args.Q) {
+                    const uint32_t tp = args.tuples[r];
+                    int tup[8];
+                    bool okr = true;
+#pragma unroll
+                    for (int m = 0; m < 7; ++m) {
+                        tup[m] = (int)((tp >> (8 * (m & 3))) & 255u);
+                        if (m < N - 1) okr &= tup[m] < args.nm;
+                    }
+                    int pin = 0;
+#pragma unroll
+                    for (int m = 0; m < 7; ++m)
+                        if (m == N - 2) pin = tup[m];
+                    const int pre = N >= 3 ? (int)tuple_rank(tup, N - 2, args.cnt, n) : 0;
+                    v = okr ? (pin | (pre << 8)) : -1;
+                }
+                ((int*)rowinfo)[rl] = v;
             }
             if (fastdiv && grp == 2) {
                 int den = 1, run = 1, r1 = 1;
@@ -1091,6 +1141,14 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 #pragma unroll
                 for (int m = 0; m < 7; ++m)
                     if (m == N - 2) pin = dg[m];
+                int pre = -1;  // compact rows: the prefix weight's rank, applied per element
+                bool rok = row_ok;
+                if (args.cmp) {
+                    const int v = ((const int*)rowinfo)[rl];
+                    rok = v >= 0;
+                    pin = v & 255;
+                    pre = N >= 3 ? (v >> 8) : -1;
+                }
                 const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
                 for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
                     uint32_t rv[4][4], iv[4][4];
@@ -1107,12 +1165,19 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         pi[c] = {0.f, 0.f};
                         const dfl vr = level_sum_df(rv[0][c], rv[1][c], rv[2][c], rv[3][c]);
                         const dfl vi = level_sum_df(iv[0][c], iv[1][c], iv[2][c], iv[3][c]);
-                        if (row_ok && qc < args.ncv && (vr.hi != 0.f || vi.hi != 0.f)) {
+                        if (rok && qc < args.ncv && (vr.hi != 0.f || vi.hi != 0.f)) {
                             const int sc = ea + colEb[cl] - VEXP + 30;
                             const dfl gr = {ldexpf(vr.hi, sc), ldexpf(vr.lo, sc)};
                             const dfl gi = {ldexpf(vi.hi, sc), ldexpf(vi.lo, sc)};
                             const float4 w = args.psi_df[(int64_t)pin * n + qc];
-                            const dfl wr = {w.x, w.y}, wi = {w.z, w.w};
+                            dfl wr = {w.x, w.y}, wi = {w.z, w.w};
+                            if (pre >= 0) {   // times prod_{m <= N-2} W[p_m][k] of the row
+                                const float4 x = args.wpre[(int64_t)pre * n + qc];
+                                const dfl xr = {x.x, x.y}, xi = {x.z, x.w};
+                                const dfl tr = df_add(df_mul(wr, xr), df_neg(df_mul(wi, xi)));
+                                wi = df_add(df_mul(wr, xi), df_mul(wi, xr));
+                                wr = tr;
+                            }
                             pr[c] = df_add(df_mul(gr, wr), df_neg(df_mul(gi, wi)));
                             pi[c] = df_add(df_mul(gr, wi), df_mul(gi, wr));
                         }
@@ -1203,7 +1268,12 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         }
                         if (args.colmask && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
                         if (no_write) continue;
-                        const int64_t rowp = row_base + (int64_t)qc * rperq;
+                        int64_t rowp = row_base + (int64_t)qc * rperq;
+                        if (MODE == EPI_DIVIDE && args.cmp) {   // compact reduction row, if sorted
+                            const int rk = ((const int*)red)[cl];
+                            if (rk < 0) continue;
+                            rowp = outer * args.RT + rk;
+                        }
                         const int key = colE[64 * sb + cl];
                         const int E = key ? key - 8192 : EXP_NONE;
                         uint32_t w[S];
@@ -1280,10 +1350,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         const int64_t rb = row0 + ((int64_t)b << lg);
                         int d0[8];
                         row_digits(row_in_outer(args, rb), N - 1, lg, d0);
-                        double2 wgt = make_double2(1.0, 0.0);
+                        double2 wgt = make_double2(1.0, 0.0);   // compact rows: applied already
 #pragma unroll
                         for (int m = 0; m < 6; ++m)
-                            if (m < N - 2) wgt = cmul(wgt, args.V[(int64_t)d0[m] * n + qc]);
+                            if (m < N - 2 && !args.cmp) wgt = cmul(wgt, args.V[(int64_t)d0[m] * n + qc]);
                         const int i = args.i0 + (int)outer_of(args, rb);
                         const double2 v = cmul(make_double2(df_to_d(ar), df_to_d(ai)), wgt);
                         atomicAdd(&args.out_f64[(int64_t)i * n + qc].x, -v.x);
@@ -1433,6 +1503,27 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
 #pragma unroll
                     for (int s = 0; s < S; ++s) dst[s * plane_stride_u32 + 32 * t] = w[t][s];
         } while (next_ordering(ord, nd));
+    }
+}
+
+// Prefix weights of the compact reduction: out[t][k] = prod_{m < M} W[p_m][k] for the t-th sorted
+// M-tuple (p_0..p_{M-1}) (8 bits per index in tup[t]), FP64 products stored as double-float
+// complex (Re hi, Re lo, Im hi, Im lo).
+__global__ void k_prefix_weights(int M, int n, int64_t count, const uint32_t* __restrict__ tup,
+                                 const double2* __restrict__ W, float4* __restrict__ out)
+{
+    const int64_t tot = count * n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = idx / n;
+        const int k = (int)(idx % n);
+        double2 w = make_double2(1.0, 0.0);
+        for (int m = 0; m < M; ++m) {
+            const int pm = (int)((tup[t] >> (8 * m)) & 255u);
+            w = cmul(w, W[(int64_t)pm * n + k]);
+        }
+        const float rh = (float)w.x, ih = (float)w.y;
+        out[idx] = make_float4(rh, (float)(w.x - rh), ih, (float)(w.y - ih));
     }
 }
 
@@ -1894,6 +1985,27 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
 
 static double factorial(int N) { double f = 1; for (int t = 2; t <= N; ++t) f *= t; return f; }
 
+// so.prefixes[M]: the non-decreasing (M-1)-tuples over [0, n) in lexicographic order, 8 bits per
+// index (M - 1 = 0: one empty tuple).
+static void ensure_tuples(Plan& p, SplitOperand& so, int M)
+{
+    if (so.prefixes[M]) return;
+    std::vector<uint32_t> pre;
+    std::vector<int> t(std::max(M - 1, 0), 0);
+    while (true) {
+        uint32_t pk = 0;
+        for (int m = 0; m < M - 1; ++m) pk |= (uint32_t)t[m] << (8 * m);
+        pre.push_back(pk);
+        int m = M - 2;
+        while (m >= 0 && t[m] == p.n - 1) --m;
+        if (m < 0) break;
+        ++t[m];
+        for (int r = m + 1; r < M - 1; ++r) t[r] = t[m];
+    }
+    so.prefixes[M] = upload(pre);
+    so.nprefix[M] = (int64_t)pre.size();
+}
+
 // Device memory of one order: S (FP64, n x P), records (n x P x 32 B), and per i of a batch two
 // operand buffers of R^(N-1) rows x 2R K' x S planes (BF16) plus exponents, R = 2^lg the row
 // radix.
@@ -1904,22 +2016,11 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     if (W) prepare_weights(p, so, W);
     set_smem_attrs<S>();
     prepare_tensor<S>(p, so, N);
-    if (!so.prefixes[N]) {   // non-decreasing (N-1)-tuples over [0, n), lexicographic
-        std::vector<uint32_t> pre;
-        std::vector<int> t(N - 1, 0);
-        while (true) {
-            uint32_t pk = 0;
-            for (int m = 0; m < N - 1; ++m) pk |= (uint32_t)t[m] << (8 * m);
-            pre.push_back(pk);
-            int m = N - 2;
-            while (m >= 0 && t[m] == p.n - 1) --m;
-            if (m < 0) break;
-            ++t[m];
-            for (int r = m + 1; r < N - 1; ++r) t[r] = t[m];
-        }
-        so.prefixes[N] = upload(pre);
-        so.nprefix[N] = (int64_t)pre.size();
-    }
+    ensure_tuples(p, so, N);
+    // compact reduction rows (order >= 3, row radix 128): sorted (N-1)-tuples per upper index
+    const int lg_run = p.n <= 32 ? 5 : p.n <= 64 ? 6 : 7;
+    const bool cmp = lg_run == 7 && N >= 3 && prefix == nullptr;
+    if (cmp) ensure_tuples(p, so, N - 1);
     int* const err = p.err_override ? p.err_override : so.err;   // a batch zeroes and checks its own
     if (!p.err_override) NPF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), p.stream));
     const int n = p.n;
@@ -1947,8 +2048,13 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const int64_t t_rows = ((int64_t)ib * npN1 + NP - 1) / NP * NP;
     const size_t tbytes = (size_t)t_rows * 2 * rad * 2 * S;
     const size_t ebytes = (size_t)t_rows * 4;
+    // compact reduction: RT rows per upper index, and the prefix weights of its rows
+    const int64_t Qc = so.nprefix[N];
+    const int64_t RTc = (Qc + NP - 1) / NP * NP;
+    const int64_t Q2 = cmp ? so.nprefix[N - 1] : 0;
+    const size_t wbytes = cmp && N >= 4 ? (size_t)Q2 * n * sizeof(float4) : 0;
     Arena& ar = p.scratch();
-    ar.reserve(s_bytes + rec_bytes + 2 * (tbytes + ebytes) + 8 * 256 + 1024);
+    ar.reserve(s_bytes + rec_bytes + 2 * (tbytes + ebytes) + wbytes + 8 * 256 + 1024);
     uint8_t* base = (uint8_t*)ar.base;
     auto take = [&](size_t bytes) { uint8_t* r = base; base += (bytes + 255) & ~(size_t)255; return r; };
     double2* Sd = (double2*)take(s_bytes);
@@ -1956,6 +2062,20 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     int* sE = (int*)take(256 * sizeof(int));
     __nv_bfloat16* T[2] = {(__nv_bfloat16*)take(tbytes), (__nv_bfloat16*)take(tbytes)};
     int* E[2] = {(int*)take(ebytes), (int*)take(ebytes)};
+    // order 3: the prefix weight is W itself (the double-float copy); order 4: pairs' products
+    const float4* wpre = nullptr;
+    if (cmp) {
+        if (N >= 4) {
+            float4* wp = (float4*)take(wbytes);
+            LaunchScope ls(&p.prof, "split_prefix_weights", p.stream);
+            k_prefix_weights<<<1024, 256, 0, p.stream>>>(N - 2, n, Q2, so.prefixes[N - 1],
+                                                         W ? W : p.d_V, wp);
+            NPF_CUDA(cudaGetLastError());
+            wpre = wp;
+        } else {
+            wpre = W ? so.w_df : so.psi_df;
+        }
+    }
 
     // a slab entry whose accumulator is exactly zero is not stored, so the slab starts at zero
     launch_zero(p, d_out, (int64_t)n * n);
@@ -2050,6 +2170,10 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
                 a.out_f64 = d_out;
                 launch_rows<S, EPI_SLAB>(p, "split_mode_divide", *tT[cb], tPhi, 2 * n, a);
             } else {
+                a.cmp = cmp;
+                a.Q = Qc;
+                a.RT = RTc;
+                a.cnt = p.d_cnt;
                 launch_rows<S, EPI_DIVIDE>(p, "split_mode_divide", *tT[cb], tPhi, 2 * n, a);
             }
             cb ^= 1;
@@ -2063,11 +2187,17 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
         a.ea = E[cb];
         a.ea_shift = 0;
         a.eb = W ? so.wred_e : so.red_e;
-        a.num_tiles = rows / NP * a.ncol_tiles;
+        a.num_tiles = (cmp ? (int64_t)cur * RTc : rows) / NP * a.ncol_tiles;
         a.digits = 1;
         a.rp = N - 1;
         a.colmask = 0;
-        a.R = npN1;
+        a.R = cmp ? RTc : npN1;
+        a.cmp = cmp;
+        a.Q = Qc;
+        a.RT = RTc;
+        a.cnt = p.d_cnt;
+        a.tuples = so.prefixes[N];
+        a.wpre = wpre;
         a.npc = rad;
         a.i0 = i0;
         a.nouter = cur;
