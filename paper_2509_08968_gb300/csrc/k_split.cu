@@ -429,6 +429,8 @@ struct RowArgs {
     const uint32_t* tuples;  // the sorted (N-1)-tuples in rank order, 8 bits per index
     const float4* wpre;      // prod_{m <= N-2} W[p_m][k] per sorted (N-2)-tuple (rank) and k,
                              // as double-float complex
+    const int* tiles;        // the tiles that run (nullptr: every tile, skipped ones tested)
+    const unsigned* ntiles_run;   // their count
     int npc;             // extent of the new index in the output layout
     int lg;              // log2 of the row radix (digits, and the next operand's K extent)
     int n;               // states (range of the a digits and of the reduction's columns k)
@@ -626,6 +628,34 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r
 //   warps 2..17      : epilogue (lane quarter = warp % 4, column group = (warp - 2) / 4). Values
 //                      needed twice (a column exponent before slicing) are read from TMEM twice
 //                      instead of being staged in shared memory.
+// The tiles of a launch that run (tile_skipped false), compacted: each block scans 256
+// consecutive tiles and appends the running ones in order at a position taken with one atomic.
+// The persistent kernel then walks this list: a skipped tile cost each of its roles a decode
+// (2.7 skipped tiles per running one in the divide stage of order 4).
+__global__ void k_tile_list(RowArgs a, int lg, int* __restrict__ list, unsigned* __restrict__ count)
+{
+    __shared__ unsigned wsum[8];
+    __shared__ unsigned base;
+    const int64_t tile = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    bool run = false;
+    if (tile < a.num_tiles) {
+        const int ct = (int)(tile & (a.ncol_tiles - 1));
+        const int64_t row0 = (tile >> a.lgncol) * NP;
+        run = !tile_skipped(a, lg, row0, ct);
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const unsigned bal = __ballot_sync(0xffffffffu, run);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int w = 0; w < 8; ++w) { const unsigned c = wsum[w]; wsum[w] = tot; tot += c; }
+        base = tot ? atomicAdd(count, tot) : 0u;
+    }
+    __syncthreads();
+    if (run) list[base + wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = (int)tile;
+}
+
 static_assert(sizeof(tfl) == 12 && 6144 + 128 * sizeof(tfl) <= 7680, "table layout");
 static_assert(7680 + 128 * sizeof(RowInfo) + 1024 <= 19 * 1024, "tables and alignment slack");
 
@@ -662,6 +692,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     const int bnr = 2 * bnc;
     const uint32_t b_bytes_tile = (uint32_t)bnr * BKm * 2;
     const int64_t ntiles = args.num_tiles;
+    // tiles walked by every role: the running-tile list when there is one
+    const int64_t nloop = args.tiles ? (int64_t)*(volatile const unsigned*)args.ntiles_run : ntiles;
     const int ncol = args.ncol_tiles;
     const int lg = SUBB ? args.lg : 7;         // row radix 2^lg (sub-blocks only below 128)
 
@@ -694,10 +726,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             // (no hold), or two: level 3 (every plane), then levels 0..2 (planes 0..2)
             uint32_t it = 0;
             bool alive = true;
-            for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+            for (int64_t k = blockIdx.x; k < nloop && alive; k += gridDim.x) {
+                const int64_t tile = args.tiles ? (int64_t)args.tiles[k] : k;
                 const int ct = (int)(tile & (ncol - 1));
                 const int64_t row0 = (tile >> args.lgncol) * NP;
-                if (tile_skipped(args, lg, row0, ct)) continue;
+                if (!args.tiles && tile_skipped(args, lg, row0, ct)) continue;
                 const int bc = ct * bnc;
                 const int k0 = first_chunk(args, lg, row0, BKm);
                 for (int pass = TWO ? 1 : 0; pass <= (TWO ? 2 : 0) && alive; ++pass) {
@@ -741,10 +774,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             const uint32_t b16 = b_bytes_tile >> 4;   // B plane stride in 16-byte units
             uint32_t it = 0, t = 0;
             bool alive = true;
-            for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+            for (int64_t k = blockIdx.x; k < nloop && alive; k += gridDim.x) {
+                const int64_t tile = args.tiles ? (int64_t)args.tiles[k] : k;
                 const int ct = (int)(tile & (ncol - 1));
                 const int64_t row0 = (tile >> args.lgncol) * NP;
-                if (tile_skipped(args, lg, row0, ct)) continue;
+                if (!args.tiles && tile_skipped(args, lg, row0, ct)) continue;
                 const int k0 = first_chunk(args, lg, row0, BKm);
                 for (int pass = TWO ? 1 : 0; pass <= (TWO ? 2 : 0) && alive; ++pass) {
                     uint64_t* gate = pass == 1 ? t3empty : tempty;
@@ -807,10 +841,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         constexpr int NGRP = EPI_WARPS / 4;                 // column groups per lane quarter
         const int N = args.N, n = args.n;
         uint32_t t = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int64_t k = blockIdx.x; k < nloop; k += gridDim.x) {
+            const int64_t tile = args.tiles ? (int64_t)args.tiles[k] : k;
             const int ct = (int)(tile & (ncol - 1));
             const int64_t row0 = (tile >> args.lgncol) * NP;
-            if (tile_skipped(args, lg, row0, ct)) continue;
+            if (!args.tiles && tile_skipped(args, lg, row0, ct)) continue;
             unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
             const int qbase = ct * bnc;
             const int64_t o = row0 + rl;                      // local row of the launch
@@ -1538,6 +1573,9 @@ struct SplitOperand {
     __nv_bfloat16* red = nullptr;   int* red_e = nullptr;    // Psi^T rows k, complex K (p)
     float4* psi_df = nullptr;
     float* lam_t = nullptr;         // lambda_p as exact triple-floats [n][Re a, b, c, Im a, b, c]
+    int* tile_list = nullptr;       // running tiles of the current launch (k_tile_list)
+    unsigned* tile_count = nullptr;
+    int64_t tile_cap = 0;
     // per order: A^T digit planes (rows Q, K' = j) and row exponents
     __nv_bfloat16* at[kMaxOrder + 1] = {};
     int* at_e[kMaxOrder + 1] = {};
@@ -1702,6 +1740,8 @@ void split_release(Plan& p)
     cudaFree(so->red); cudaFree(so->red_e);
     cudaFree(so->psi_df);
     cudaFree(so->lam_t);
+    cudaFree(so->tile_list);
+    cudaFree(so->tile_count);
     for (int N = 0; N <= kMaxOrder; ++N) { cudaFree(so->at[N]); cudaFree(so->at_e[N]); }
     cudaFree(so->wred); cudaFree(so->wred_e); cudaFree(so->w_df);
     for (int N = 0; N <= kMaxOrder; ++N) cudaFree(so->prefixes[N]);
@@ -1951,6 +1991,28 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
     a.klast = (kprime + KSTEP - 1) / KSTEP - (bk / KSTEP) * (a.kch - 1);
     const TMaps tA = plane_maps<S>(A, bk);
     const TMaps tB = fixed_maps<S>(B, a.bnc, bk);
+    // the running tiles, listed on the device (stream order puts the list before the launch)
+    SplitOperand& so = *p.split;
+    if (!so.tile_list || so.tile_cap < a.num_tiles) {
+        if (p.capturing) fail(NPF_ERR_CUDA, "tile list would grow during graph capture");
+        cudaFree(so.tile_list);
+        cudaFree(so.tile_count);
+        so.tile_list = nullptr;
+        so.tile_count = nullptr;
+        NPF_CUDA(cudaMalloc(&so.tile_list, (size_t)a.num_tiles * sizeof(int)));
+        NPF_CUDA(cudaMalloc(&so.tile_count, sizeof(unsigned)));
+        so.tile_cap = a.num_tiles;
+    }
+    if (a.num_tiles >= (int64_t)1 << 31) fail(NPF_ERR_UNSUPPORTED, "too many tiles in one launch");
+    NPF_CUDA(cudaMemsetAsync(so.tile_count, 0, sizeof(unsigned), p.stream));
+    {
+        LaunchScope ls(&p.prof, "split_tile_list", p.stream);
+        k_tile_list<<<(unsigned)((a.num_tiles + 255) / 256), 256, 0, p.stream>>>(a, a.lg, so.tile_list,
+                                                                                so.tile_count);
+        NPF_CUDA(cudaGetLastError());
+    }
+    a.tiles = so.tile_list;
+    a.ntiles_run = so.tile_count;
     static const bool tracing = getenv("NPF_TRACE_TILES") != nullptr;
     unsigned long long* dtrace = nullptr;
     if (tracing) {
