@@ -577,6 +577,22 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
     }
 }
 
+// Whether the slice pair (s, u) belongs to a pass (PASS 0: every pair; 1: level 3; 2: levels 0..2).
+__host__ __device__ constexpr bool pair_in_pass(int pass, int s, int u)
+{
+    return pass == 0 || (pass == 1) == (s + u >= 3);
+}
+
+template <bool ACC>
+__device__ __forceinline__ void mma_col(int col, uint32_t d, uint32_t a, uint32_t b, uint32_t hi,
+                                        uint32_t idesc)
+{
+    if (col == 1) tc::mma_bf16_lohi_col<ACC, 1>(d, a, b, hi, idesc);
+    else if (col == 2) tc::mma_bf16_lohi_col<ACC, 2>(d, a, b, hi, idesc);
+    else if (col == 3) tc::mma_bf16_lohi_col<ACC, 3>(d, a, b, hi, idesc);
+    else tc::mma_bf16_lohi<ACC>(d, a, b, hi, idesc);
+}
+
 // One K' step of MMAs: the slice pairs (s, u), s + u < S, of one pass into their level
 // accumulators. PASS 0: every pair (no hold); PASS 1: the level-3 pairs (s + u >= 3); PASS 2: the
 // pairs of levels 0..2. FIRST: the step opens the pass, so each level's first MMA overwrites
@@ -584,6 +600,10 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
 // offsets (start address / 16 in the low half).
 // NKS: MMA K steps issued from the stage (32-byte K offsets within a 64-byte swizzled row; 1 when
 // the stage's second half is padding). The descriptor's swizzle matches the stage width.
+// The MMAs that share a data plane s and K step run back to back over the fixed-matrix planes u,
+// with the data tile held in the tensor core's collector buffer: shared memory delivers each
+// data tile once per (s, K step) instead of once per pair (M = N = 128 MMAs otherwise read 8 KB
+// of operands per 64 cycles, which the measured MMA rate showed to be the limit).
 template <int S, int MODE, int PASS, bool FIRST, int NKS>
 __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_lo, uint32_t b_lo,
                                             uint32_t b_plane16, uint32_t idesc)
@@ -592,21 +612,28 @@ __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_lo, uint32
     constexpr uint32_t hi = C::BK == 32 ? tc::kSdescSw64Hi : tc::kSdescSw32Hi;
     bool first[4] = {FIRST, FIRST, FIRST, FIRST};
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s) {
+        int nu = 0;   // pairs of this pass on data plane s
 #pragma unroll
-        for (int u = 0; u < S - s; ++u) {
-            const int L = s + u < 3 ? s + u : 3;
-            if (PASS == 1 && L != 3) continue;
-            if (PASS == 2 && L == 3) continue;
+        for (int u = 0; u < S - s; ++u) nu += pair_in_pass(PASS, s, u) ? 1 : 0;
 #pragma unroll
-            for (int ks = 0; ks < NKS; ++ks) {
-                const uint32_t ao = a_lo + (uint32_t)((s * C::A_TILE + ks * 32) >> 4);
+        for (int ks = 0; ks < NKS; ++ks) {
+            const uint32_t ao = a_lo + (uint32_t)((s * C::A_TILE + ks * 32) >> 4);
+            int j = 0;
+#pragma unroll
+            for (int u = 0; u < S - s; ++u) {
+                if (!pair_in_pass(PASS, s, u)) continue;
+                const int L = s + u < 3 ? s + u : 3;
                 const uint32_t bo = b_lo + (uint32_t)u * b_plane16 + (uint32_t)(ks * 2);
-                if (first[L]) tc::mma_bf16_lohi<false>(tmem + L * 128, ao, bo, hi, idesc);
-                else tc::mma_bf16_lohi<true>(tmem + L * 128, ao, bo, hi, idesc);
+                // collector: fill on the first MMA of the run, release on the last
+                const int col = nu == 1 ? 0 : j == 0 ? 1 : j == nu - 1 ? 3 : 2;
+                if (first[L]) mma_col<false>(col, tmem + L * 128, ao, bo, hi, idesc);
+                else mma_col<true>(col, tmem + L * 128, ao, bo, hi, idesc);
                 first[L] = false;
+                ++j;
             }
         }
+    }
 }
 
 // Planes a pass reads (level 3 needs every plane; levels 0..2 only planes 0..2).

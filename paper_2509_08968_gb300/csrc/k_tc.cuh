@@ -172,6 +172,27 @@ __device__ __forceinline__ void mma_bf16_lohi(uint32_t d_tmem, uint32_t a_lo, ui
         "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "n"(ACC ? 1 : 0)
         : "memory");
 }
+// The same MMA with the A operand kept in the tensor core's collector buffer across consecutive
+// MMAs that read the same A tile: COL 1 fills it (and reads A from shared memory), 2 reads it from
+// the buffer, 3 reads it from the buffer and releases it; 0 reads A from shared memory only.
+#define NPF_MMA_COL(OP)                                                                          \
+    asm volatile("{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"                                  \
+                 "mov.b64 da, {%1, %3};\n\t"                                                      \
+                 "mov.b64 db, {%2, %3};\n\t"                                                      \
+                 "setp.ne.b32 p, %5, 0;\n\t"                                                      \
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::" OP " [%0], da, db, %4, p;\n\t}" \
+                 ::"r"(d_tmem), "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "n"(ACC ? 1 : 0)       \
+                 : "memory")
+template <bool ACC, int COL>
+__device__ __forceinline__ void mma_bf16_lohi_col(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
+                                                  uint32_t hi, uint32_t idesc)
+{
+    if constexpr (COL == 0) mma_bf16_lohi<ACC>(d_tmem, a_lo, b_lo, hi, idesc);
+    else if constexpr (COL == 1) NPF_MMA_COL("fill");
+    else if constexpr (COL == 2) NPF_MMA_COL("use");
+    else NPF_MMA_COL("lastuse");
+}
+#undef NPF_MMA_COL
 // Shared-memory matrix descriptor of a K-major operand stored with the 64-byte swizzle (rows of 32
 // BF16 = 64 bytes, 8-row atoms of 512 bytes), as two 32-bit halves: start address >> 4 at bits
 // 0-13, leading byte offset (unused for swizzled K-major, 1) at 16-29; stride byte offset =
