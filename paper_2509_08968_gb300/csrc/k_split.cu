@@ -492,7 +492,7 @@ struct RowCfg {
     // barriers, column tables, reduction partials and row tables (< 17 KB), and 1 KB of
     // alignment slack
     static constexpr int TABLES = 19 * 1024;
-    static_assert(2 * 8 * 8 + 3 * 8 + 8 <= 256, "barriers fit the first 256 bytes of the tables");
+    static_assert(2 * 8 * 8 + 5 * 8 + 8 <= 256, "barriers fit the first 256 bytes of the tables");
     static constexpr int SMEM_MAX = 227 * 1024;
     static constexpr int STAGES_FIT = (SMEM_MAX - TABLES - HOLD_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
@@ -584,13 +584,13 @@ __host__ __device__ constexpr bool pair_in_pass(int pass, int s, int u)
 }
 
 template <bool ACC>
-__device__ __forceinline__ void mma_col(int col, uint32_t d, uint32_t a, uint32_t b, uint32_t hi,
-                                        uint32_t idesc)
+__device__ __forceinline__ void mma_col(int col, uint32_t leader, uint32_t d, uint32_t a, uint32_t b,
+                                        uint32_t hi, uint32_t idesc)
 {
-    if (col == 1) tc::mma_bf16_lohi_col<ACC, 1>(d, a, b, hi, idesc);
-    else if (col == 2) tc::mma_bf16_lohi_col<ACC, 2>(d, a, b, hi, idesc);
-    else if (col == 3) tc::mma_bf16_lohi_col<ACC, 3>(d, a, b, hi, idesc);
-    else tc::mma_bf16_lohi<ACC>(d, a, b, hi, idesc);
+    if (col == 1) tc::mma_bf16_lohi<ACC, 1>(leader, d, a, b, hi, idesc);
+    else if (col == 2) tc::mma_bf16_lohi<ACC, 2>(leader, d, a, b, hi, idesc);
+    else if (col == 3) tc::mma_bf16_lohi<ACC, 3>(leader, d, a, b, hi, idesc);
+    else tc::mma_bf16_lohi<ACC, 0>(leader, d, a, b, hi, idesc);
 }
 
 // One K' step of MMAs: the slice pairs (s, u), s + u < S, of one pass into their level
@@ -598,6 +598,7 @@ __device__ __forceinline__ void mma_col(int col, uint32_t d, uint32_t a, uint32_
 // pairs of levels 0..2. FIRST: the step opens the pass, so each level's first MMA overwrites
 // instead of accumulating. The loops unroll into straight-line MMAs with constant descriptor
 // offsets (start address / 16 in the low half).
+// Level L accumulates at TMEM column tmem + L * lstride.
 // NKS: MMA K steps issued from the stage (32-byte K offsets within a 64-byte swizzled row; 1 when
 // the stage's second half is padding). The descriptor's swizzle matches the stage width.
 // The MMAs that share a data plane s and K step run back to back over the fixed-matrix planes u,
@@ -605,8 +606,9 @@ __device__ __forceinline__ void mma_col(int col, uint32_t d, uint32_t a, uint32_
 // data tile once per (s, K step) instead of once per pair (M = N = 128 MMAs otherwise read 8 KB
 // of operands per 64 cycles, which the measured MMA rate showed to be the limit).
 template <int S, int MODE, int PASS, bool FIRST, int NKS>
-__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_lo, uint32_t b_lo,
-                                            uint32_t b_plane16, uint32_t idesc)
+__device__ __forceinline__ void issue_kstep(uint32_t leader, uint32_t tmem, uint32_t lstride,
+                                            uint32_t a_lo, uint32_t b_lo, uint32_t b_plane16,
+                                            uint32_t idesc)
 {
     using C = RowCfg<S, MODE>;
     constexpr uint32_t hi = C::BK == 32 ? tc::kSdescSw64Hi : tc::kSdescSw32Hi;
@@ -627,8 +629,8 @@ __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_lo, uint32
                 const uint32_t bo = b_lo + (uint32_t)u * b_plane16 + (uint32_t)(ks * 2);
                 // collector: fill on the first MMA of the run, release on the last
                 const int col = nu == 1 ? 0 : j == 0 ? 1 : j == nu - 1 ? 3 : 2;
-                if (first[L]) mma_col<false>(col, tmem + L * 128, ao, bo, hi, idesc);
-                else mma_col<true>(col, tmem + L * 128, ao, bo, hi, idesc);
+                if (first[L]) mma_col<false>(col, leader, tmem + L * lstride, ao, bo, hi, idesc);
+                else mma_col<true>(col, leader, tmem + L * lstride, ao, bo, hi, idesc);
                 first[L] = false;
                 ++j;
             }
@@ -698,13 +700,13 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     uint8_t* stage_base = smem;
     float4* hold = (float4*)(smem + C::STAGES * C::STAGE_BYTES);   // level-3 hold (S >= 4)
     // tables at fixed offsets from a 1 KB boundary: barriers and the TMEM slot in the first
-    // 256 bytes (at most 2 x 8 + 3 barriers), then each table 16-byte aligned
+    // 256 bytes (at most 2 x 8 + 5 barriers), then each table 16-byte aligned
     uint8_t* tables = smem + C::STAGES * C::STAGE_BYTES + C::HOLD_BYTES;
     uint64_t* full = (uint64_t*)tables;
     uint64_t* empty = full + C::STAGES;
-    uint64_t* tfull = empty + C::STAGES;       // MMA -> epilogue: accumulators complete
-    uint64_t* tempty = tfull + 1;              // epilogue -> MMA: levels 0..2 (all, no hold) read
-    uint64_t* t3empty = tempty + 1;            // epilogue -> MMA: level 3 copied to the hold
+    uint64_t* tfull = empty + C::STAGES;       // [2] MMA -> epilogue: accumulators complete
+    uint64_t* tempty = tfull + 2;              // [2] epilogue -> MMA: levels 0..2 (all, no hold) read
+    uint64_t* t3empty = tempty + 2;            // epilogue -> MMA: level 3 copied to the hold
     uint32_t* tmem_slot = (uint32_t*)(t3empty + 1);
     int* stop = (int*)(tmem_slot + 1);
     int* colE = (int*)(tables + 256);          // [4 sub-blocks][64] column exponent keys
@@ -722,6 +724,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     // tiles walked by every role: the running-tile list when there is one
     const int64_t nloop = args.tiles ? (int64_t)*(volatile const unsigned*)args.ntiles_run : ntiles;
     const int ncol = args.ncol_tiles;
+    // TMEM accumulator sets: two when one tile's levels fit in half of TMEM (single-pass modes,
+    // 2 * bnc <= 64 real columns a level), so that the MMAs of the next tile run during this
+    // tile's epilogue; tile t uses set t % nset, its levels lstride columns apart
+    const int nset = (!TWO && Lev<S>::N * bnr <= TMEM_COLS / 2) ? 2 : 1;
+    const uint32_t lstride = nset == 2 ? (uint32_t)bnr : 128u;
     const int lg = SUBB ? args.lg : 7;         // row radix 2^lg (sub-blocks only below 128)
 
     if (threadIdx.x == 0) {
@@ -729,8 +736,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(tfull, 1);
-        tc::mbar_init(tempty, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], 1);
+        }
         tc::mbar_init(t3empty, EPI_WARPS);     // one arrival per epilogue warp
         tc::fence_mbar_init();
         tc::tma_prefetch(&tmA.all);
@@ -792,11 +801,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        {
             // ---------------- MMA issuer: slice pairs (s, t), s + t < S, accumulated by level.
             // With the hold, the level-3 pass of a tile starts once the epilogue has copied the
             // previous tile's level 3 out of TMEM, and the pass of levels 0..2 once the epilogue
             // has finished the previous tile.
+            // The whole warp runs this loop (waits made warp-uniform by a vote), so that the
+            // descriptor arithmetic stays uniform; one elected lane issues the MMAs and commits.
+            // Issued from a one-lane branch, each MMA cost ~75 cycles whatever its N.
+            const uint32_t leader = tc::elect_one();
             const uint32_t idesc = tc::idesc_bf16_f32(128, bnr);
             const uint32_t b16 = b_bytes_tile >> 4;   // B plane stride in 16-byte units
             uint32_t it = 0, t = 0;
@@ -807,9 +820,12 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const int64_t row0 = (tile >> args.lgncol) * NP;
                 if (!args.tiles && tile_skipped(args, lg, row0, ct)) continue;
                 const int k0 = first_chunk(args, lg, row0, BKm);
+                const int set = nset == 2 ? (int)(t & 1) : 0;
+                const uint32_t use = nset == 2 ? t >> 1 : t;     // earlier tiles on this set
+                const uint32_t tm = tmem + (uint32_t)set * (TMEM_COLS / 2);
                 for (int pass = TWO ? 1 : 0; pass <= (TWO ? 2 : 0) && alive; ++pass) {
-                    uint64_t* gate = pass == 1 ? t3empty : tempty;
-                    if (!tc::mbar_wait(gate, (t & 1) ^ 1, args.err, kErrTimeout)) {
+                    uint64_t* gate = pass == 1 ? t3empty : &tempty[set];
+                    if (!__all_sync(0xffffffffu, tc::mbar_wait(gate, (use & 1) ^ 1, args.err, kErrTimeout))) {
                         alive = false;
                         break;
                     }
@@ -818,7 +834,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     for (int kc = k0; kc < args.kch; kc += kstride, ++it) {
                         const int st = (int)(it % C::STAGES);
                         const uint32_t ph = (it / C::STAGES) & 1;
-                        if (!tc::mbar_wait(&full[st], ph, args.err, kErrTimeout)) {
+                        if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[st], ph, args.err, kErrTimeout))) {
                             alive = false;
                             break;
                         }
@@ -828,33 +844,33 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         const uint32_t b_lo = tc::sdesc_sw64_lo(aBase + S * C::A_TILE);
                         if constexpr (TWO) {
                             if (pass == 1) {
-                                if (kc == k0) issue_kstep<S, MODE, 1, true, 1>(tmem, a_lo, b_lo, b16, idesc);
-                                else issue_kstep<S, MODE, 1, false, 1>(tmem, a_lo, b_lo, b16, idesc);
+                                if (kc == k0) issue_kstep<S, MODE, 1, true, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                else issue_kstep<S, MODE, 1, false, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
                             } else {
                                 constexpr int np2 = pass_planes<S>(2);
                                 const int nks = min(kstride, args.kch - kc);
                                 for (int j = 0; j < nks; ++j) {
                                     const uint32_t aj = a_lo + (uint32_t)(j * np2 * C::A_TILE / 16);
                                     const uint32_t bj = b_lo + (uint32_t)(j * np2) * b16;
-                                    if (kc == k0 && j == 0) issue_kstep<S, MODE, 2, true, 1>(tmem, aj, bj, b16, idesc);
-                                    else issue_kstep<S, MODE, 2, false, 1>(tmem, aj, bj, b16, idesc);
+                                    if (kc == k0 && j == 0) issue_kstep<S, MODE, 2, true, 1>(leader, tm, lstride, aj, bj, b16, idesc);
+                                    else issue_kstep<S, MODE, 2, false, 1>(leader, tm, lstride, aj, bj, b16, idesc);
                                 }
                             }
                         } else {
                             const bool half = kc == args.kch - 1 && args.klast == 1;
                             if (kc == k0) {
-                                if (half) issue_kstep<S, MODE, 0, true, 1>(tmem, a_lo, b_lo, b16, idesc);
-                                else issue_kstep<S, MODE, 0, true, Pipe<S, MODE>::KS>(tmem, a_lo, b_lo, b16, idesc);
+                                if (half) issue_kstep<S, MODE, 0, true, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                else issue_kstep<S, MODE, 0, true, Pipe<S, MODE>::KS>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
                             } else {
-                                if (half) issue_kstep<S, MODE, 0, false, 1>(tmem, a_lo, b_lo, b16, idesc);
-                                else issue_kstep<S, MODE, 0, false, Pipe<S, MODE>::KS>(tmem, a_lo, b_lo, b16, idesc);
+                                if (half) issue_kstep<S, MODE, 0, false, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                else issue_kstep<S, MODE, 0, false, Pipe<S, MODE>::KS>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
                             }
                         }
-                        tc::mma_commit(&empty[st]);
+                        tc::mma_commit(leader, &empty[st]);
                     }
                 }
                 if (!alive) break;
-                if (!args.stall) tc::mma_commit(tfull);
+                if (!args.stall) tc::mma_commit(leader, &tfull[set]);
                 ++t;
             }
         }
@@ -864,7 +880,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         const int q4 = warp % 4;                            // TMEM lane quarter of this warp
         const int grp = (warp - 2) / 4;                     // column group (EPI_WARPS / 4 groups)
         const int rl = q4 * 32 + lane;                      // local row within the tile
-        const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
+        const uint32_t trow0 = tmem + ((uint32_t)(q4 * 32) << 16);
         constexpr int NGRP = EPI_WARPS / 4;                 // column groups per lane quarter
         const int N = args.N, n = args.n;
         uint32_t t = 0;
@@ -1096,7 +1112,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 trc[4] = blockIdx.x + 1;
             }
             // warp-uniform (the epilogue's shuffles and TMEM loads are warp-collective)
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(tfull, t & 1, args.err, kErrTimeout));
+            const int set = nset == 2 ? (int)(t & 1) : 0;
+            const uint32_t use = nset == 2 ? t >> 1 : t;
+            const uint32_t trow = trow0 + (uint32_t)set * (TMEM_COLS / 2);
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&tfull[set], use & 1, args.err, kErrTimeout));
             tc::fence_after_sync();
             // this thread's level-3 slots of the hold: Re columns of unit u at slot u, Im at 4 + u
             float4* held = hold + ((size_t)grp * 8 * NP + rl);
@@ -1104,8 +1123,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 // level 3 out of TMEM first, so that the next tile's level-3 MMAs can start
                 for (int u = 0; u < cols / 4; ++u) {
                     uint32_t r3[4], i3[4];
-                    tc::tmem_ld4(trow + 3 * 128 + cbeg + 4 * u, r3);
-                    tc::tmem_ld4(trow + bnc + 3 * 128 + cbeg + 4 * u, i3);
+                    tc::tmem_ld4(trow + 3 * lstride + cbeg + 4 * u, r3);
+                    tc::tmem_ld4(trow + bnc + 3 * lstride + cbeg + 4 * u, i3);
                     tc::tmem_wait_ld();
                     held[(size_t)u * NP] = make_float4(__uint_as_float(r3[0]), __uint_as_float(r3[1]),
                                                        __uint_as_float(r3[2]), __uint_as_float(r3[3]));
@@ -1151,9 +1170,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
                         uint32_t rv[2][4], iv[2][4];   // levels 0 and 1 only
                         tc::tmem_ld4(trow + c4, rv[0]);
-                        tc::tmem_ld4(trow + c4 + 128, rv[1]);
+                        tc::tmem_ld4(trow + c4 + lstride, rv[1]);
                         tc::tmem_ld4(trow + bnc + c4, iv[0]);
-                        tc::tmem_ld4(trow + bnc + c4 + 128, iv[1]);
+                        tc::tmem_ld4(trow + bnc + c4 + lstride, iv[1]);
                         tc::tmem_wait_ld();
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -1215,8 +1234,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
                     uint32_t rv[4][4], iv[4][4];
                     const int u = (c4 - cbeg) / 4;
-                    load_levels<S, TWO>(trow + c4, 128, rv, held + (size_t)u * NP);
-                    load_levels<S, TWO>(trow + bnc + c4, 128, iv, held + (size_t)(4 + u) * NP);
+                    load_levels<S, TWO>(trow + c4, lstride, rv, held + (size_t)u * NP);
+                    load_levels<S, TWO>(trow + bnc + c4, lstride, iv, held + (size_t)(4 + u) * NP);
                     tc::tmem_wait_ld();
                     dfl pr[4], pi[4];
 #pragma unroll
@@ -1288,8 +1307,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 for (int c4 = cbeg; c4 < cbeg + cols; c4 += 4) {
                     uint32_t rv[4][4], iv[4][4];
                     const int u = (c4 - cbeg) / 4;
-                    load_levels<S, TWO>(trow + c4, 128, rv, held + (size_t)u * NP);
-                    load_levels<S, TWO>(trow + bnc + c4, 128, iv, held + (size_t)(4 + u) * NP);
+                    load_levels<S, TWO>(trow + c4, lstride, rv, held + (size_t)u * NP);
+                    load_levels<S, TWO>(trow + bnc + c4, lstride, iv, held + (size_t)(4 + u) * NP);
                     tc::tmem_wait_ld();
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -1426,7 +1445,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             tc::fence_before_sync();
             epi_sync();
             if (trc && et == 0) trc[3] = global_ns();
-            if (et == 0) tc::mbar_arrive(tempty);
+            if (et == 0) tc::mbar_arrive(&tempty[set]);
             ++t;
         }
     }

@@ -155,44 +155,46 @@ __device__ __forceinline__ void tmem_wait_ld()
 }
 
 // ---------------------------------------------------------------------------- MMA
-// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulation, issued by one thread; the
-// shared-memory descriptors are given as 32-bit halves (low: start address and leading offset,
-// high: stride offset, version, layout) and the accumulate flag is fixed, so that a loop of MMAs
-// over one stage costs a 32-bit add per operand and the instruction.
-template <bool ACC>
-__device__ __forceinline__ void mma_bf16_lohi(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
-                                              uint32_t hi, uint32_t idesc)
+// 1 on one lane of the (converged) warp, 0 on the others.
+__device__ __forceinline__ uint32_t elect_one()
 {
+    uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
-        "mov.b64 da, {%1, %3};\n\t"
-        "mov.b64 db, {%2, %3};\n\t"
-        "setp.ne.b32 p, %5, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "n"(ACC ? 1 : 0)
-        : "memory");
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r));
+    return r;
 }
-// The same MMA with the A operand kept in the tensor core's collector buffer across consecutive
-// MMAs that read the same A tile: COL 1 fills it (and reads A from shared memory), 2 reads it from
-// the buffer, 3 reads it from the buffer and releases it; 0 reads A from shared memory only.
-#define NPF_MMA_COL(OP)                                                                          \
-    asm volatile("{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"                                  \
-                 "mov.b64 da, {%1, %3};\n\t"                                                      \
-                 "mov.b64 db, {%2, %3};\n\t"                                                      \
-                 "setp.ne.b32 p, %5, 0;\n\t"                                                      \
-                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::" OP " [%0], da, db, %4, p;\n\t}" \
-                 ::"r"(d_tmem), "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "n"(ACC ? 1 : 0)       \
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulation. The whole issuing warp runs
+// the call (its descriptor arithmetic stays warp-uniform) and the lane with `leader` != 0 issues
+// the MMA. The shared-memory descriptors are given as 32-bit halves (low: start address and
+// leading offset, high: stride offset, version, layout) and the accumulate flag is fixed, so that
+// a loop of MMAs over one stage costs a 32-bit add per operand and the instruction.
+// COL keeps the A operand in the tensor core's collector buffer across consecutive MMAs that read
+// the same A tile: 1 fills it (reading A from shared memory), 2 reads it from the buffer, 3 reads
+// it from the buffer and releases it; 0 reads A from shared memory only.
+#define NPF_MMA(QUAL)                                                                           \
+    asm volatile("{\n\t.reg .pred p, q;\n\t.reg .b64 da, db;\n\t"                              \
+                 "mov.b64 da, {%1, %3};\n\t"                                                     \
+                 "mov.b64 db, {%2, %3};\n\t"                                                     \
+                 "setp.ne.b32 p, %5, 0;\n\t"                                                     \
+                 "setp.ne.b32 q, %6, 0;\n\t"                                                     \
+                 "@q tcgen05.mma.cta_group::1.kind::f16" QUAL " [%0], da, db, %4, p;\n\t}"         \
+                 ::"r"(d_tmem), "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "n"(ACC ? 1 : 0),     \
+                 "r"(leader)                                                                    \
                  : "memory")
 template <bool ACC, int COL>
-__device__ __forceinline__ void mma_bf16_lohi_col(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
-                                                  uint32_t hi, uint32_t idesc)
+__device__ __forceinline__ void mma_bf16_lohi(uint32_t leader, uint32_t d_tmem, uint32_t a_lo,
+                                              uint32_t b_lo, uint32_t hi, uint32_t idesc)
 {
-    if constexpr (COL == 0) mma_bf16_lohi<ACC>(d_tmem, a_lo, b_lo, hi, idesc);
-    else if constexpr (COL == 1) NPF_MMA_COL("fill");
-    else if constexpr (COL == 2) NPF_MMA_COL("use");
-    else NPF_MMA_COL("lastuse");
+    if constexpr (COL == 0) NPF_MMA("");
+    else if constexpr (COL == 1) NPF_MMA(".collector::a::fill");
+    else if constexpr (COL == 2) NPF_MMA(".collector::a::use");
+    else NPF_MMA(".collector::a::lastuse");
 }
-#undef NPF_MMA_COL
+#undef NPF_MMA
 // Shared-memory matrix descriptor of a K-major operand stored with the 64-byte swizzle (rows of 32
 // BF16 = 64 bytes, 8-row atoms of 512 bytes), as two 32-bit halves: start address >> 4 at bits
 // 0-13, leading byte offset (unused for swizzled K-major, 1) at 16-29; stride byte offset =
@@ -207,12 +209,15 @@ constexpr uint32_t kSdescSw64Hi = (512u >> 4) | (1u << 14) | (4u << 29);
 // byte offset 256 >> 4, layout type SWIZZLE_32B = 6.
 constexpr uint32_t kSdescSw32Hi = (256u >> 4) | (1u << 14) | (6u << 29);
 
-// Arrive once on `bar` when every tcgen05.mma issued so far by this thread has completed.
-__device__ __forceinline__ void mma_commit(uint64_t* bar)
+// Arrive once on `bar` when every tcgen05.mma issued so far by the leader lane has completed
+// (issued by the leader lane of the warp that issued them).
+__device__ __forceinline__ void mma_commit(uint32_t leader, uint64_t* bar)
 {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.b32 q, %1, 0;\n\t"
+        "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+        ::"r"(smem_u32(bar)), "r"(leader)
         : "memory");
 }
 
