@@ -2030,6 +2030,16 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
                         RowArgs a)
 {
     constexpr int bk = RowCfg<S, MODE>::BK;
+    if (Pipe<S, MODE>::two && a.bnc < 64) {
+        // two-pass tiles keep one TMEM accumulator set and the level-3 hold, so a narrower tile
+        // only adds MMA issues (an M = 128 MMA costs ~55 cycles at N <= 64, 64 at N = 128): they
+        // run 64 complex columns wide (or the whole radix) whatever the tuned width
+        const int rad = a.bnc * a.ncol_tiles;
+        const int wide = rad < 64 ? rad : 64;
+        a.num_tiles = a.num_tiles / a.ncol_tiles * (rad / wide);
+        a.ncol_tiles = rad / wide;
+        a.bnc = wide;
+    }
     a.kch = (kprime + bk - 1) / bk;            // K' past kprime holds zeros on both sides
     a.lgR = (a.R > 0 && (a.R & (a.R - 1)) == 0) ? __builtin_ctzll((unsigned long long)a.R) : -1;
     a.lgncol = __builtin_ctz((unsigned)a.ncol_tiles);
@@ -2141,8 +2151,8 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const int lg = n <= 32 ? 5 : n <= 64 ? 6 : 7;
     const int rad = 1 << lg;
     const int64_t npN1 = ipow64(rad, N - 1);
-    // complex columns per tile (the slab path runs untuned: 64 when the plan autotunes)
-    const int bnc = std::min(p.tile_n > 0 ? p.tile_n : 64, rad);
+    // complex columns per tile (the slab path runs untuned: 32 when the plan autotunes)
+    const int bnc = std::min(p.tile_n > 0 ? p.tile_n : 32, rad);
     const bool slab = prefix != nullptr;
 
     // ---- memory plan (Algorithm 1's rule on the upper-index space)

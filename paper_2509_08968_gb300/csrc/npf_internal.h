@@ -77,7 +77,7 @@ struct Plan {
     int fp64_quotient = 0;         // tensor-core divide epilogue: 1 = native FP64 quotient
     int debug_stall = 0;           // test hook of the timeout path (NPF_OPT_DEBUG_STALL)
     int row_lo = 0, row_hi = -1;   // upper-index rows of Psi_N to compute (-1: all)
-    int tile_n = 64;               // complex columns per tensor-core tile; 0 = autotuned
+    int tile_n = 32;               // complex columns per tensor-core tile; 0 = autotuned
     size_t mem_budget = 0;         // 0 = 80% of free memory at compute time
     cudaStream_t stream = nullptr;
     Profiler prof;
