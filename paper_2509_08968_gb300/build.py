@@ -15,7 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["npf_api.cu", "k_common.cu", "k_fp64.cu", "k_split.cu", "k_mlp.cu", "k_model.cu"]
+SOURCES = ["npf_api.cu", "k_common.cu", "k_fp64.cu", "k_split.cu", "k_split_low.cu", "k_mlp.cu",
+           "k_model.cu"]
+# sources that include another source file
+INCLUDES = {"k_split_low.cu": ["k_split.cu"]}
 HEADERS = ["npf_internal.h", "k_device.cuh", "k_tc.cuh"]
 
 
@@ -43,7 +46,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(OBJ, src.replace(".cu", ".o"))
-        if force or _stale(o, [s] + hdrs + [__file__]):
+        extra = [os.path.join(CSRC, d) for d in INCLUDES.get(src, [])]
+        if force or _stale(o, [s] + extra + hdrs + [__file__]):
             jobs.append([nvcc] + flags + ["-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:

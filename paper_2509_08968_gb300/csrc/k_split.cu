@@ -645,15 +645,19 @@ __host__ __device__ constexpr int pass_planes(int pass) { return pass == 2 ? (S 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory"); }
 
 // Persistent row GEMM: one CTA per SM walks the tiles blockIdx.x, +gridDim.x, ... Roles:
-//   warp 0 (one lane): TMA producer over a ring of STAGES shared-memory stages (one 16-wide K'
-//                      step each) that runs across tiles, so the next tile's operands stream in
-//                      during this tile's epilogue;
-//   warp 1 (one lane): MMA issuer. All 512 TMEM columns hold the four level accumulators of one
-//                      128 x bnc-complex tile. With four levels a tile runs in two passes over K:
-//                      first the 15 level-3 slice pairs (S = 6), then the 6 pairs of levels 0..2.
-//                      The epilogue copies level 3 to a shared-memory hold as soon as the tile is
-//                      complete, so the next tile's level-3 pass (most of its MMAs) overlaps the
-//                      rest of this tile's epilogue; only the levels-0..2 pass waits for it;
+//   warp 0 (one lane): TMA producer over a ring of STAGES shared-memory stages (16 or 32 K'
+//                      each) that runs across tiles, so the next tile's operands stream in during
+//                      this tile's epilogue;
+//   warp 1           : MMA issuer (the warp runs the loop, one elected lane issues). The four
+//                      level accumulators of a 128 x bnc-complex tile take 8 bnc TMEM columns.
+//                      One-pass modes at bnc <= 32 alternate two accumulator sets, so the next
+//                      tile's MMAs run during this tile's epilogue; at bnc = 64 they fill TMEM and
+//                      wait for it. The divide and the reduction (four levels) run two passes
+//                      over K: first the 15 level-3 slice pairs (S = 6), then the 6 pairs of
+//                      levels 0..2. The epilogue copies level 3 to a shared-memory hold as soon as
+//                      the tile is complete, so the next tile's level-3 pass (most of its MMAs)
+//                      overlaps the rest of this tile's epilogue; only the levels-0..2 pass waits
+//                      for it;
 //   warps 2..17      : epilogue (lane quarter = warp % 4, column group = (warp - 2) / 4). Values
 //                      needed twice (a column exponent before slicing) are read from TMEM twice
 //                      instead of being staged in shared memory.
@@ -661,7 +665,7 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r
 // consecutive tiles and appends the running ones in order at a position taken with one atomic.
 // The persistent kernel then walks this list: a skipped tile cost each of its roles a decode
 // (2.7 skipped tiles per running one in the divide stage of order 4).
-__global__ void k_tile_list(RowArgs a, int lg, int* __restrict__ list, unsigned* __restrict__ count)
+static __global__ void k_tile_list(RowArgs a, int lg, int* __restrict__ list, unsigned* __restrict__ count)
 {
     __shared__ unsigned wsum[8];
     __shared__ unsigned base;
@@ -1460,7 +1464,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 // ---------------------------------------------------------------------------------------
 // Digit records of S^i_Q (per upper index i, exponent over all Q) for the dense expansion.
 // ---------------------------------------------------------------------------------------
-__global__ void k_s_exp(const double2* __restrict__ Sd, int64_t ld, int64_t P, int* __restrict__ E)
+static __global__ void k_s_exp(const double2* __restrict__ Sd, int64_t ld, int64_t P, int* __restrict__ E)
 {
     const int i = blockIdx.x;
     double m = 0.0;
@@ -1590,7 +1594,7 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
 // Prefix weights of the compact reduction: out[t][k] = prod_{m < M} W[p_m][k] for the t-th sorted
 // M-tuple (p_0..p_{M-1}) (8 bits per index in tup[t]), FP64 products stored as double-float
 // complex (Re hi, Re lo, Im hi, Im lo).
-__global__ void k_prefix_weights(int M, int n, int64_t count, const uint32_t* __restrict__ tup,
+static __global__ void k_prefix_weights(int M, int n, int64_t count, const uint32_t* __restrict__ tup,
                                  const double2* __restrict__ W, float4* __restrict__ out)
 {
     const int64_t tot = count * n;
@@ -1777,6 +1781,7 @@ static T* upload(const std::vector<T>& v)
     return d;
 }
 
+#ifndef NPF_SPLIT_LOW
 void split_release(Plan& p)
 {
     SplitOperand* so = p.split;
@@ -1795,6 +1800,7 @@ void split_release(Plan& p)
     delete so;
     p.split = nullptr;
 }
+#endif
 
 template <int S, int MODE, bool SUBB>
 static void smem_attr()
@@ -1910,10 +1916,12 @@ static void prepare_weights(Plan& p, SplitOperand& so, const double2* dW)
     put(so.w_df, wdf);
 }
 
+#ifndef NPF_SPLIT_LOW
 void split_refresh_modes(Plan& p)
 {
     if (p.split) fill_fixed(p, p.split);   // same n and S: the buffers (and graphs) stay valid
 }
+#endif
 
 // A^T digit planes of the packed tensor (part of the tensor upload; redone when the tensor or the
 // slice count changes).
@@ -1942,6 +1950,7 @@ static void prepare_tensor(Plan& p, SplitOperand& so, int N)
     so.at_src[N] = p.d_tensor[N];
 }
 
+#ifndef NPF_SPLIT_LOW
 void split_forget_tensor(Plan& p, int N)
 {
     if (p.split) p.split->at_src[N] = nullptr;
@@ -1966,6 +1975,7 @@ void split_prepare_tensor(Plan& p, int N)
     default: break;
     }
 }
+#endif
 
 // Tracing aid: with NPF_TRACE_TILES set in the environment every k_rows launch records per-CTA
 // phase times (%globaltimer) and prints the median phase durations to stderr.
@@ -2329,21 +2339,34 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     if (herr) fail(NPF_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
 }
 
-static void split_any(Plan& p, int N, double2* d_out, const int* prefix, const double2* W)
+// The 2..5-slice runs live in a second translation unit (k_split_low.cu, these sources compiled
+// with NPF_SPLIT_LOW), so that the kernel instantiations of the two halves build in parallel.
+void split_run_low(Plan& p, int S, int N, double2* d_out, const int* prefix, const double2* W);
+
+#ifdef NPF_SPLIT_LOW
+void split_run_low(Plan& p, int S, int N, double2* d_out, const int* prefix, const double2* W)
 {
-    if (N < 1 || (N == 1 && !prefix)) fail(NPF_ERR_ARG, "order must be >= 2 (order 1: modal slabs only)");
-    if (N > 4) fail(NPF_ERR_UNSUPPORTED, "the tensor-core path supports orders <= 4 (use NPF_PREC_FP64)");
-    switch (default_slices(p)) {
+    switch (S) {
     case 2: split_run<2>(p, N, d_out, prefix, W); break;
     case 3: split_run<3>(p, N, d_out, prefix, W); break;
     case 4: split_run<4>(p, N, d_out, prefix, W); break;
     case 5: split_run<5>(p, N, d_out, prefix, W); break;
-    case 6: split_run<6>(p, N, d_out, prefix, W); break;
     default: fail(NPF_ERR_UNSUPPORTED, "slices must be in [2, 6] on the tensor-core path");
     }
+}
+#else
+static void split_any(Plan& p, int N, double2* d_out, const int* prefix, const double2* W)
+{
+    if (N < 1 || (N == 1 && !prefix)) fail(NPF_ERR_ARG, "order must be >= 2 (order 1: modal slabs only)");
+    if (N > 4) fail(NPF_ERR_UNSUPPORTED, "the tensor-core path supports orders <= 4 (use NPF_PREC_FP64)");
+    const int S = default_slices(p);
+    if (S == 6) split_run<6>(p, N, d_out, prefix, W);
+    else if (S >= 2 && S <= 5) split_run_low(p, S, N, d_out, prefix, W);
+    else fail(NPF_ERR_UNSUPPORTED, "slices must be in [2, 6] on the tensor-core path");
 }
 
 void split_term(Plan& p, int N, double2* d_out, const double2* W) { split_any(p, N, d_out, nullptr, W); }
 void split_slab(Plan& p, int N, const int* prefix, double2* d_out) { split_any(p, N, d_out, prefix, nullptr); }
+#endif
 
 }  // namespace npf
