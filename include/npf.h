@@ -265,7 +265,7 @@ int64_t npf_launch_count(void);
  * process exits); a problem whose scratch does not fit (all of 2 n^N + n^(N-1) complex values for
  * one output-index batch, plus small tables) is rejected with NPF_ERR_UNSUPPORTED before any
  * work. The first call on a device looks up the array's device address (set-up, once per
- * device), so make that first call before any stream capture begins. All calls share the array
+ * device). All calls share the array
  * and it keeps the last call's contents (every call rebuilds what it reads), so calls that
  * overlap on the GPU race on it. */
 int npf_term_fp64_noalloc(int n, int order, const npf_c128* eigvals, const npf_c128* U,

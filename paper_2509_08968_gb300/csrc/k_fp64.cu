@@ -327,7 +327,7 @@ void fp64_slab(Plan& p, int N, const int* prefix, double2* d_out)
 // which every device that loads this library keeps until the process exits. Host code must not
 // pass `g_noalloc_scratch` itself to a kernel (on the host that name is only a stand-in); the
 // device address comes from cudaGetSymbolAddress, looked up once per device by the first call
-// made with that device current -- make that first call before any stream capture.
+// made with that device current.
 // Every call shares the one array: calls that overlap on the GPU (other streams, other host
 // threads) race on it.
 // ---------------------------------------------------------------------------------------
