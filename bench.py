@@ -294,7 +294,7 @@ def main():
     ap.add_argument("--cpu-sample", type=float, default=0.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile-n", type=int, default=0,
-                    help="complex columns per tensor-core tile (16/32/64; 0 = library default)")
+                    help="complex columns per tensor-core tile (16/32/48/64; 0 = library default)")
     ap.add_argument("--modes", type=int, default=0,
                     help="critical-mode subset: the m least-damped modes (0 = all modes)")
     ap.add_argument("--mem-budget", type=float, default=0.0,

@@ -76,14 +76,16 @@ enum npf_option {
                                sum_p C^i_p prod_m psi_{p_m k} = (1/N!) sum_j psi_ij A^j_{k..k}. */
     NPF_OPT_MEM_BUDGET = 5, /* bytes of device memory for intermediates; 0 = 80% of free memory. */
     NPF_OPT_PROFILE = 6,    /* 1: time each kernel launch with CUDA events (npf_get_profile). */
-    NPF_OPT_TILE_N = 7,     /* complex columns per tensor-core tile: 16, 32 (default) or 64, or
+    NPF_OPT_TILE_N = 7,     /* complex columns per tensor-core tile: 16, 32 (default), 48 or 64, or
                                0 = autotuned: the first term of each (n, order, precision,
                                slices, divide) times every width on the plan's own work and the
                                fastest is kept for the process (npf_tuned_tile). The width
                                applies to the one-pass contractions (upper index, mode
                                products, slabs; at 32 or less they alternate two accumulator
-                               sets); with 4 or more slices the divide and the reduction run
-                               two passes over K and keep 64 (32 when n <= 32). */
+                               sets); 48 runs the mode products of the 4- and 6-slice forms at
+                               n > 64 in 48-column tiles with two passes over K and a level-3
+                               hold (32 elsewhere); with 4 or more slices the divide and the
+                               reduction run two passes over K and keep 64 (32 when n <= 32). */
     NPF_OPT_FP64_QUOTIENT = 8, /* tensor-core forms, Alg. 2 steps 5-11: 1 = form h = C / D with
                                native FP64 arithmetic; 0 (default) = the denominator
                                D = lambda_p1 + .. + lambda_pN - lambda_i exactly from FP64 inputs

@@ -389,7 +389,12 @@ __global__ void k_prep_at(const double* __restrict__ A, int64_t P, int n,
 // column <= first p when `colmask`) and the padding (digits >= n) decide which tiles run (a tile
 // runs when any sub-block does) and which elements count.
 // ---------------------------------------------------------------------------------------
-enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3, EPI_REDUCE = 4 };
+enum { EPI_F64T = 0, EPI_SLICE = 1, EPI_DIVIDE = 2, EPI_SLAB = 3, EPI_REDUCE = 4, EPI_SLICEH = 5 };
+// EPI_SLICEH: the mode products' re-slicing epilogue on 48-column tiles (N = 96, three column
+// tiles per 128-wide radix) with the level-3 hold and two passes over K. An MMA at N = 96 costs
+// ~56 cycles against ~55 at N = 64 and 64 at N = 128 (back-to-back MMAs, M = 128, K = 16), and
+// the hold lets the level-3 pass of the next tile (15 of the 21 slice pairs) run beside the epilogue.
+__host__ __device__ constexpr bool is_slice(int mode) { return mode == EPI_SLICE || mode == EPI_SLICEH; }
 
 // Tensor maps of one operand: every slice plane in one box (`all`), and the planes of levels
 // 0..2 only (`low`, the second pass of a tile with the level-3 hold).
@@ -419,7 +424,7 @@ struct RowArgs {
                          // (orders <= 4 have at most two shared a's)
     int64_t R;           // rows per outer index (output layout [outer][q][r])
     int lgR;             // log2(R) when R is a power of two (digit rows), else -1
-    int lgncol;          // log2(ncol_tiles)
+    int lgncol;          // log2(ncol_tiles), or -1 when ncol_tiles is not a power of two
     // compact reduction rows (order >= 3, row radix 128): the reduction's operand rows are the
     // sorted tuples (i, p_1 <= .. <= p_{N-1}) in lexicographic rank, RT rows per upper index (Q of
     // them valid, then padding to whole tiles). EPI_DIVIDE writes them, EPI_REDUCE reads them.
@@ -473,8 +478,10 @@ __device__ __forceinline__ unsigned long long global_ns()
 // fast as TMA refills shared memory, and a second pass would re-read planes 0..2.
 template <int S, int MODE>
 struct Pipe {
-    static constexpr bool two = Lev<S>::N == 4 && (MODE == EPI_DIVIDE || MODE == EPI_REDUCE);
-    static constexpr int BK = two ? 16 : 32;     // K' elements per stage
+    static constexpr bool two = Lev<S>::N == 4 && (MODE == EPI_DIVIDE || MODE == EPI_REDUCE || MODE == EPI_SLICEH);
+    // K' elements per stage: 16 (32-byte rows) where the 64 KB hold leaves three 48 KB stages,
+    // 32 (64-byte rows) otherwise (the 48-column tiles: two 84 KB stages beside a 48 KB hold)
+    static constexpr int BK = (two && MODE != EPI_SLICEH) ? 16 : 32;
     static constexpr int KS = BK / KSTEP;        // MMA K steps per stage
     // K steps per stage of the second pass, which reads planes 0..2 only: as many as the
     // stage's S plane slots hold, so the ring keeps as many bytes in flight as in the first pass
@@ -485,24 +492,36 @@ template <int S, int MODE>
 struct RowCfg {
     static constexpr int BK = Pipe<S, MODE>::BK;
     static constexpr int A_TILE = NP * BK * 2;                 // 4 or 8 KB
-    static constexpr int B_TILE = NP * BK * 2;                 // up to 128 rows
+    // fixed-matrix rows of a stage: 2 x 48 at N = 96 (EPI_SLICEH), else up to 128
+    static constexpr int BROWS = MODE == EPI_SLICEH ? 96 : NP;
+    static constexpr int B_TILE = BROWS * BK * 2;
     static constexpr int STAGE_BYTES = S * (A_TILE + B_TILE);
     // level-3 hold: [4 column groups][8 float4 slots][128 rows]
-    static constexpr int HOLD_BYTES = Pipe<S, MODE>::two ? 4 * 8 * NP * 16 : 0;
+    // level-3 hold: [4 column groups][HSLOT float4 slots][128 rows]; a thread holds the Re and Im
+    // level-3 values of its column units (up to 4 at 64 columns, 3 at 48)
+    static constexpr int HSLOT = MODE == EPI_SLICEH ? 6 : 8;
+    static constexpr int HOLD_BYTES = Pipe<S, MODE>::two ? 4 * HSLOT * NP * 16 : 0;
     // barriers, column tables, reduction partials and row tables (< 17 KB), and 1 KB of
     // alignment slack
-    static constexpr int TABLES = 19 * 1024;
+    // (the re-slicing epilogue uses only the barriers and the column tables)
+    static constexpr int TABLES = is_slice(MODE) ? 3 * 1024 : 19 * 1024;
     static_assert(2 * 8 * 8 + 5 * 8 + 8 <= 256, "barriers fit the first 256 bytes of the tables");
     static constexpr int SMEM_MAX = 227 * 1024;
     static constexpr int STAGES_FIT = (SMEM_MAX - TABLES - HOLD_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
     static constexpr int SMEM = STAGES * STAGE_BYTES + HOLD_BYTES + TABLES;
-    static_assert(STAGES >= 3 || (!Pipe<S, MODE>::two && STAGES >= 2), "pipeline stages");
+    static_assert(STAGES >= 3 || ((!Pipe<S, MODE>::two || MODE == EPI_SLICEH) && STAGES >= 2), "pipeline stages");
     static_assert(SMEM <= SMEM_MAX, "shared memory");
 };
 
 // Compact reduction input: the reduction launch (kfrom) with compact rows.
 #define MODE_IS_COMPACT_INPUT(a) ((a).cmp && (a).kfrom)
+// Column tile and first local row of a tile index (tiles are ordered row block major).
+__device__ __forceinline__ void tile_pos(const RowArgs& a, int64_t tile, int& ct, int64_t& row0)
+{
+    if (a.lgncol >= 0) { ct = (int)(tile & (a.ncol_tiles - 1)); row0 = (tile >> a.lgncol) * NP; }
+    else { const int64_t rb = tile / a.ncol_tiles; ct = (int)(tile - rb * a.ncol_tiles); row0 = rb * NP; }
+}
 
 // Row index within / across the outer index (shifts for the power-of-two digit layouts: 64-bit
 // divisions by a runtime divisor cost ~70 instructions, and every role decodes every tile).
@@ -672,8 +691,7 @@ static __global__ void k_tile_list(RowArgs a, int lg, int* __restrict__ list, un
     const int64_t tile = (int64_t)blockIdx.x * 256 + threadIdx.x;
     bool run = false;
     if (tile < a.num_tiles) {
-        const int ct = (int)(tile & (a.ncol_tiles - 1));
-        const int64_t row0 = (tile >> a.lgncol) * NP;
+        int ct; int64_t row0; tile_pos(a, tile, ct, row0);
         run = !tile_skipped(a, lg, row0, ct);
     }
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -691,6 +709,7 @@ static __global__ void k_tile_list(RowArgs a, int lg, int* __restrict__ list, un
 
 static_assert(sizeof(tfl) == 12 && 6144 + 128 * sizeof(tfl) <= 7680, "table layout");
 static_assert(7680 + 128 * sizeof(RowInfo) + 1024 <= 19 * 1024, "tables and alignment slack");
+static_assert(1280 + 64 * 4 + 1024 <= 3 * 1024, "re-slicing tables (barriers, colE, colEb) and alignment slack");
 
 template <int S, int MODE, bool SUBB>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
@@ -727,7 +746,6 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     const int64_t ntiles = args.num_tiles;
     // tiles walked by every role: the running-tile list when there is one
     const int64_t nloop = args.tiles ? (int64_t)*(volatile const unsigned*)args.ntiles_run : ntiles;
-    const int ncol = args.ncol_tiles;
     // TMEM accumulator sets: two when one tile's levels fit in half of TMEM (single-pass modes,
     // 2 * bnc <= 64 real columns a level), so that the MMAs of the next tile run during this
     // tile's epilogue; tile t uses set t % nset, its levels lstride columns apart
@@ -768,8 +786,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             bool alive = true;
             for (int64_t k = blockIdx.x; k < nloop && alive; k += gridDim.x) {
                 const int64_t tile = args.tiles ? (int64_t)args.tiles[k] : k;
-                const int ct = (int)(tile & (ncol - 1));
-                const int64_t row0 = (tile >> args.lgncol) * NP;
+                int ct; int64_t row0; tile_pos(args, tile, ct, row0);
                 if (!args.tiles && tile_skipped(args, lg, row0, ct)) continue;
                 const int bc = ct * bnc;
                 const int k0 = first_chunk(args, lg, row0, BKm);
@@ -820,8 +837,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             bool alive = true;
             for (int64_t k = blockIdx.x; k < nloop && alive; k += gridDim.x) {
                 const int64_t tile = args.tiles ? (int64_t)args.tiles[k] : k;
-                const int ct = (int)(tile & (ncol - 1));
-                const int64_t row0 = (tile >> args.lgncol) * NP;
+                int ct; int64_t row0; tile_pos(args, tile, ct, row0);
                 if (!args.tiles && tile_skipped(args, lg, row0, ct)) continue;
                 const int k0 = first_chunk(args, lg, row0, BKm);
                 const int set = nset == 2 ? (int)(t & 1) : 0;
@@ -847,17 +863,33 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         const uint32_t a_lo = tc::sdesc_sw64_lo(aBase);
                         const uint32_t b_lo = tc::sdesc_sw64_lo(aBase + S * C::A_TILE);
                         if constexpr (TWO) {
+                            // KS MMA K steps a chunk (1 at 16-wide chunks; 2 at 32-wide ones, 1
+                            // for a last chunk that is half padding)
+                            constexpr int KSm = Pipe<S, MODE>::KS;
                             if (pass == 1) {
-                                if (kc == k0) issue_kstep<S, MODE, 1, true, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
-                                else issue_kstep<S, MODE, 1, false, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                const bool half = KSm > 1 && kc == args.kch - 1 && args.klast == 1;
+                                if (kc == k0) {
+                                    if (half) issue_kstep<S, MODE, 1, true, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                    else issue_kstep<S, MODE, 1, true, KSm>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                } else {
+                                    if (half) issue_kstep<S, MODE, 1, false, 1>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                    else issue_kstep<S, MODE, 1, false, KSm>(leader, tm, lstride, a_lo, b_lo, b16, idesc);
+                                }
                             } else {
                                 constexpr int np2 = pass_planes<S>(2);
                                 const int nks = min(kstride, args.kch - kc);
                                 for (int j = 0; j < nks; ++j) {
                                     const uint32_t aj = a_lo + (uint32_t)(j * np2 * C::A_TILE / 16);
                                     const uint32_t bj = b_lo + (uint32_t)(j * np2) * b16;
-                                    if (kc == k0 && j == 0) issue_kstep<S, MODE, 2, true, 1>(leader, tm, lstride, aj, bj, b16, idesc);
-                                    else issue_kstep<S, MODE, 2, false, 1>(leader, tm, lstride, aj, bj, b16, idesc);
+                                    const bool half = KSm > 1 && kc + j == args.kch - 1 && args.klast == 1;
+                                    const bool first = kc == k0 && j == 0;
+                                    if (first) {
+                                        if (half) issue_kstep<S, MODE, 2, true, 1>(leader, tm, lstride, aj, bj, b16, idesc);
+                                        else issue_kstep<S, MODE, 2, true, KSm>(leader, tm, lstride, aj, bj, b16, idesc);
+                                    } else {
+                                        if (half) issue_kstep<S, MODE, 2, false, 1>(leader, tm, lstride, aj, bj, b16, idesc);
+                                        else issue_kstep<S, MODE, 2, false, KSm>(leader, tm, lstride, aj, bj, b16, idesc);
+                                    }
                                 }
                             }
                         } else {
@@ -890,8 +922,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         uint32_t t = 0;
         for (int64_t k = blockIdx.x; k < nloop; k += gridDim.x) {
             const int64_t tile = args.tiles ? (int64_t)args.tiles[k] : k;
-            const int ct = (int)(tile & (ncol - 1));
-            const int64_t row0 = (tile >> args.lgncol) * NP;
+            int ct; int64_t row0; tile_pos(args, tile, ct, row0);
             if (!args.tiles && tile_skipped(args, lg, row0, ct)) continue;
             unsigned long long* trc = args.trace ? args.trace + tile * 6 : nullptr;
             const int qbase = ct * bnc;
@@ -948,7 +979,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             // the non-decreasing one (its operand row was never written), so it writes nothing.
             int64_t swap_off = 0;
             bool no_write = false;
-            if (MODE == EPI_SLICE && args.aswap) {
+            if (is_slice(MODE) && args.aswap) {
                 const int j = args.rp, nd = N - 1;
                 if (j + 1 <= nd - 2) {
                     if (dg[j] < dg[j + 1]) {
@@ -1122,7 +1153,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&tfull[set], use & 1, args.err, kErrTimeout));
             tc::fence_after_sync();
             // this thread's level-3 slots of the hold: Re columns of unit u at slot u, Im at 4 + u
-            float4* held = hold + ((size_t)grp * 8 * NP + rl);
+            // (Re columns of unit u at slot u, Im at HSLOT / 2 + u)
+            constexpr int HS2 = C::HSLOT / 2;
+            float4* held = hold + ((size_t)grp * C::HSLOT * NP + rl);
             if (TWO && ok) {
                 // level 3 out of TMEM first, so that the next tile's level-3 MMAs can start
                 for (int u = 0; u < cols / 4; ++u) {
@@ -1132,7 +1165,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     tc::tmem_wait_ld();
                     held[(size_t)u * NP] = make_float4(__uint_as_float(r3[0]), __uint_as_float(r3[1]),
                                                        __uint_as_float(r3[2]), __uint_as_float(r3[3]));
-                    held[(size_t)(4 + u) * NP] = make_float4(__uint_as_float(i3[0]), __uint_as_float(i3[1]),
+                    held[(size_t)(HS2 + u) * NP] = make_float4(__uint_as_float(i3[0]), __uint_as_float(i3[1]),
                                                              __uint_as_float(i3[2]), __uint_as_float(i3[3]));
                 }
                 tc::fence_before_sync();
@@ -1163,7 +1196,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 return h;
             };
 
-            if (MODE == EPI_SLICE || MODE == EPI_DIVIDE) {
+            if (is_slice(MODE) || MODE == EPI_DIVIDE) {
                 // pass 1: column exponents (max over the tile's valid rows). For the quotients an
                 // FP32 upper bound of |h| = |V| 2^(ea+eb-VEXP) f / |D| with a lower bound of the
                 // clamped |D| (FP32 error of sigma + lambda_q bounded by 4 ulp of its terms).
@@ -1190,7 +1223,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                             const bool valid = row_ok && !no_write && qc < args.ncv &&
                                                (!args.colmask || qc <= firstp);
                             unsigned key = 0;
-                            if (MODE == EPI_SLICE) {
+                            if (is_slice(MODE)) {
                                 // bitlen(V) <= exponent(bound) + 30
                                 const float bm = fmaxf(br, bi);
                                 if (valid && bm > 0.f)
@@ -1239,7 +1272,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     uint32_t rv[4][4], iv[4][4];
                     const int u = (c4 - cbeg) / 4;
                     load_levels<S, TWO>(trow + c4, lstride, rv, held + (size_t)u * NP);
-                    load_levels<S, TWO>(trow + bnc + c4, lstride, iv, held + (size_t)(4 + u) * NP);
+                    load_levels<S, TWO>(trow + bnc + c4, lstride, iv, held + (size_t)(HS2 + u) * NP);
                     tc::tmem_wait_ld();
                     dfl pr[4], pi[4];
 #pragma unroll
@@ -1312,7 +1345,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     uint32_t rv[4][4], iv[4][4];
                     const int u = (c4 - cbeg) / 4;
                     load_levels<S, TWO>(trow + c4, lstride, rv, held + (size_t)u * NP);
-                    load_levels<S, TWO>(trow + bnc + c4, lstride, iv, held + (size_t)(4 + u) * NP);
+                    load_levels<S, TWO>(trow + bnc + c4, lstride, iv, held + (size_t)(HS2 + u) * NP);
                     tc::tmem_wait_ld();
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -1351,7 +1384,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                                 args.out_f64[(int64_t)(args.i0 + outer) * n + extra] = h;
                             continue;
                         }
-                        if (args.colmask && qc > firstp && MODE == EPI_SLICE) continue;   // unused rows
+                        if (args.colmask && qc > firstp && is_slice(MODE)) continue;   // unused rows
                         if (no_write) continue;
                         int64_t rowp = row_base + (int64_t)qc * rperq;
                         if (MODE == EPI_DIVIDE && args.cmp) {   // compact reduction row, if sorted
@@ -1365,7 +1398,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         if (key == 0 || !valid) {
 #pragma unroll
                             for (int s = 0; s < S; ++s) w[s] = 0u;
-                        } else if (MODE == EPI_SLICE) {
+                        } else if (is_slice(MODE)) {
                             const int sh = ea + eb - VEXP - E + 7 + 8 * (S - 1);
                             digit_pairs<S>(shift_round(Vr, sh), shift_round(Vi, sh), w);
                         } else if (args.fp64_quotient) {
@@ -1405,7 +1438,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 #pragma unroll
                         for (int s = 0; s < S; ++s) dst[s * (args.out_plane_stride / 2)] = w[s];
                         if (kpos == 0) args.out_exp[rowp] = E;
-                        if (MODE == EPI_SLICE && swap_off != 0) {   // the same row, shared a's swapped
+                        if (is_slice(MODE) && swap_off != 0) {   // the same row, shared a's swapped
                             uint32_t* d2 = dst + (swap_off << lg);
 #pragma unroll
                             for (int s = 0; s < S; ++s) d2[s * (args.out_plane_stride / 2)] = w[s];
@@ -1823,6 +1856,7 @@ static void set_smem_attrs()
     smem_attr<S, EPI_SLAB, true>();
     smem_attr<S, EPI_REDUCE, false>();
     smem_attr<S, EPI_REDUCE, true>();
+    if constexpr (S == 4 || S == 6) smem_attr<S, EPI_SLICEH, false>();
     done = true;
 }
 
@@ -2040,7 +2074,7 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
                         RowArgs a)
 {
     constexpr int bk = RowCfg<S, MODE>::BK;
-    if (Pipe<S, MODE>::two && a.bnc < 64) {
+    if (Pipe<S, MODE>::two && MODE != EPI_SLICEH && a.bnc < 64) {
         // two-pass tiles keep one TMEM accumulator set and the level-3 hold, so a narrower tile
         // only adds MMA issues (an M = 128 MMA costs ~55 cycles at N <= 64, 64 at N = 128): they
         // run 64 complex columns wide (or the whole radix) whatever the tuned width
@@ -2052,8 +2086,7 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
     }
     a.kch = (kprime + bk - 1) / bk;            // K' past kprime holds zeros on both sides
     a.lgR = (a.R > 0 && (a.R & (a.R - 1)) == 0) ? __builtin_ctzll((unsigned long long)a.R) : -1;
-    a.lgncol = __builtin_ctz((unsigned)a.ncol_tiles);
-    if ((a.ncol_tiles & (a.ncol_tiles - 1)) != 0) fail(NPF_ERR_ARG, "column tiles must be a power of two");
+    a.lgncol = (a.ncol_tiles & (a.ncol_tiles - 1)) == 0 ? __builtin_ctz((unsigned)a.ncol_tiles) : -1;
     a.klast = (kprime + KSTEP - 1) / KSTEP - (bk / KSTEP) * (a.kch - 1);
     const TMaps tA = plane_maps<S>(A, bk);
     const TMaps tB = fixed_maps<S>(B, a.bnc, bk);
@@ -2094,7 +2127,7 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
         int64_t grid = std::min<int64_t>(a.num_tiles, sm_count());
         if (grid > 1 && a.ncol_tiles > 1 && grid % 2 == 0) grid -= 1;
         const unsigned g = (unsigned)std::max<int64_t>(grid, 1);
-        if constexpr (MODE != EPI_F64T) {
+        if constexpr (MODE != EPI_F64T && MODE != EPI_SLICEH) {   // (48-column tiles: radix 128 only)
             if (a.lg < 7) k_rows<S, MODE, true><<<g, ROW_THREADS, RowCfg<S, MODE>::SMEM, p.stream>>>(tA, tB, a);
             else k_rows<S, MODE, false><<<g, ROW_THREADS, RowCfg<S, MODE>::SMEM, p.stream>>>(tA, tB, a);
         } else {
@@ -2161,8 +2194,13 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     const int lg = n <= 32 ? 5 : n <= 64 ? 6 : 7;
     const int rad = 1 << lg;
     const int64_t npN1 = ipow64(rad, N - 1);
-    // complex columns per tile (the slab path runs untuned: 32 when the plan autotunes)
-    const int bnc = std::min(p.tile_n > 0 ? p.tile_n : 32, rad);
+    // complex columns per tile. A width of 48 means 48-column mode-product tiles with the level-3 hold (the 4- and 6-slice
+    // forms at radix 128; three column tiles per radix) and 32 for every other launch and radix.
+    // The slab path runs untuned: 32 when the plan autotunes.
+    const int want = p.tile_n > 0 ? p.tile_n : 32;
+    bool wide48 = false;
+    if constexpr (S == 4 || S == 6) wide48 = want == 48 && lg == 7;
+    const int bnc = std::min(want == 48 ? 32 : want, rad);
     const bool slab = prefix != nullptr;
 
     // ---- memory plan (Algorithm 1's rule on the upper-index space)
@@ -2293,7 +2331,15 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
             a.out_plane_stride = t_rows * 2 * rad;
             a.out_exp = E[cb ^ 1];
             if (c < N) {
-                launch_rows<S, EPI_SLICE>(p, "split_mode_product", *tT[cb], tPhi, 2 * n, a);
+                bool done48 = false;
+                if constexpr (S == 4 || S == 6) {
+                    if (wide48) {
+                        a.bnc = 48; a.ncol_tiles = 3; a.num_tiles = rows / NP * 3;
+                        launch_rows<S, EPI_SLICEH>(p, "split_mode_product", *tT[cb], tPhi, 2 * n, a);
+                        done48 = true;
+                    }
+                }
+                if (!done48) launch_rows<S, EPI_SLICE>(p, "split_mode_product", *tT[cb], tPhi, 2 * n, a);
             } else if (slab) {
                 a.out_f64 = d_out;
                 launch_rows<S, EPI_SLAB>(p, "split_mode_divide", *tT[cb], tPhi, 2 * n, a);

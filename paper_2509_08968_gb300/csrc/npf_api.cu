@@ -193,7 +193,7 @@ void load_modes(Plan& p, const npf_c128* eigvals, const npf_c128* U, const npf_c
 using TuneKey = std::array<int, 5>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
-constexpr int kTileCandidates[3] = {16, 32, 64};
+constexpr int kTileCandidates[4] = {16, 32, 48, 64};
 
 TuneKey tune_key(const Plan& p, int N) { return {p.n, N, p.precision, p.slices, p.divide}; }
 
@@ -871,8 +871,8 @@ int npf_set_option(npf_handle* h, int key, double value)
             break;
         case NPF_OPT_TILE_N: {
             const int v = (int)value;
-            if (v != 0 && v != 16 && v != 32 && v != 64)
-                npf::fail(NPF_ERR_ARG, "tile width must be 0 (autotuned), 16, 32 or 64");
+            if (v != 0 && v != 16 && v != 32 && v != 48 && v != 64)
+                npf::fail(NPF_ERR_ARG, "tile width must be 0 (autotuned), 16, 32, 48 or 64");
             p.tile_n = v;
             break;
         }

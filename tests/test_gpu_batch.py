@@ -75,7 +75,7 @@ def test_batch_matches_oracle_and_replays(npf, systems, references):
                 assert rel_fro(b, a) < 1e-13
         # every (n, order) key was tuned to one of the candidate widths
         for sysm, N in systems:
-            assert npf.tuned_tile(sysm.lam.shape[0], N) in (16, 32, 64)
+            assert npf.tuned_tile(sysm.lam.shape[0], N) in (16, 32, 48, 64)
     finally:
         for p in plans:
             p.close()

@@ -3,8 +3,10 @@
 At 32 complex columns or fewer a one-pass launch (upper contraction, mode products) alternates two
 TMEM accumulator sets, tile t on set t mod 2 with its four levels 2 x width columns apart, so the
 next tile's MMAs run during the epilogue; at 64 columns the levels fill TMEM and the epilogue runs
-in series. The divide and the reduction (two passes over K with the level-3 hold) run 64 columns
-wide whatever the width asked for. Each width at each radix (32 for n <= 32, 64 for n <= 64, else
+in series. Width 48 runs the mode products at radix 128 in 48-column tiles (N = 96, three column
+tiles per radix) with two passes over K and the level-3 hold, and 32 elsewhere. The divide and the
+reduction (two passes over K with the level-3 hold) run 64 columns wide whatever the width asked
+for. Each width at each radix (32 for n <= 32, 64 for n <= 64, else
 128), for the FP64-emulating form (6 slices, bar 1e-10) and the FP32 form (4 slices, bar 1e-5),
 against the oracle's Psi_3; n = 68 with an odd and an even number of tiles per CTA across the
 launches of a term.
@@ -41,7 +43,7 @@ def _ref(n, sysm):
 
 
 @pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
-@pytest.mark.parametrize("width", [16, 32, 64])
+@pytest.mark.parametrize("width", [16, 32, 48, 64])
 @pytest.mark.parametrize("n", [30, 60, 68])
 def test_tile_width_matches_oracle(npf, n, width, prec):
     sysm = _system(n)
