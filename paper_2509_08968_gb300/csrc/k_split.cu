@@ -1497,11 +1497,21 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 // ---------------------------------------------------------------------------------------
 // Digit records of S^i_Q (per upper index i, exponent over all Q) for the dense expansion.
 // ---------------------------------------------------------------------------------------
+// The exponent of max_Q |S^i_Q| per upper index i: blocks (chunk, i) take strided slices of one
+// row and merge their maxima by an integer atomicMax on the frexp exponent (monotone in the
+// magnitude), so that each row spreads over several SMs. E holds EXP_NONE on entry (k_exp_init).
+static __global__ void k_exp_init(int* __restrict__ E, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) E[i] = EXP_NONE;
+}
+
 static __global__ void k_s_exp(const double2* __restrict__ Sd, int64_t ld, int64_t P, int* __restrict__ E)
 {
-    const int i = blockIdx.x;
+    const int i = blockIdx.y;
     double m = 0.0;
-    for (int64_t q = threadIdx.x; q < P; q += blockDim.x) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P;
+         q += (int64_t)gridDim.x * blockDim.x) {
         const double2 v = Sd[(int64_t)i * ld + q];
         m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
     }
@@ -1512,10 +1522,10 @@ static __global__ void k_s_exp(const double2* __restrict__ Sd, int64_t ld, int64
         if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        int e = EXP_NONE;
-        if (red[0] > 0.0) frexp(red[0], &e);
-        E[i] = e;
+    if (threadIdx.x == 0 && red[0] > 0.0) {
+        int e;
+        frexp(red[0], &e);
+        atomicMax(&E[i], e);
     }
 }
 
@@ -2294,7 +2304,11 @@ static void split_run(Plan& p, int N, double2* d_out, const int* prefix, const d
     }
     {
         LaunchScope ls(&p.prof, "split_s_records", p.stream);
-        k_s_exp<<<nm, 256, 0, p.stream>>>(Sd, Prows, P, sE);
+        // a few blocks per upper index, so that the n rows fill the GPU
+        const int64_t per_row = std::max<int64_t>(1, std::min<int64_t>((2 * sm_count() + nm - 1) / nm,
+                                                                       (P + 255) / 256));
+        k_exp_init<<<(nm + 255) / 256, 256, 0, p.stream>>>(sE, nm);
+        k_s_exp<<<dim3((unsigned)per_row, (unsigned)nm), 256, 0, p.stream>>>(Sd, Prows, P, sE);
         k_s_records<S><<<4096, 256, 0, p.stream>>>(Sd, Prows, P, nm, sE, rec);
         NPF_CUDA(cudaGetLastError());
     }
