@@ -411,7 +411,7 @@ struct RowArgs {
     const int* ea;       // row exponents, indexed by (local row) >> ea_shift
     int ea_shift;
     const int* eb;       // column exponents of the fixed matrix (256 entries)
-    int bnc;             // complex columns per tile (64)
+    int bnc;             // complex columns per tile (16, 32, 48 or 64)
     int ncol_tiles;
     int64_t num_tiles;
     int N;               // order
@@ -2085,9 +2085,11 @@ static void launch_rows(Plan& p, const char* name, const DataOp& A, const FixedO
 {
     constexpr int bk = RowCfg<S, MODE>::BK;
     if (Pipe<S, MODE>::two && MODE != EPI_SLICEH && a.bnc < 64) {
-        // two-pass tiles keep one TMEM accumulator set and the level-3 hold, so a narrower tile
-        // only adds MMA issues (an M = 128 MMA costs ~55 cycles at N <= 64, 64 at N = 128): they
-        // run 64 complex columns wide (or the whole radix) whatever the tuned width
+        // the divide's and the reduction's two-pass tiles keep one TMEM accumulator set and the
+        // level-3 hold, so a narrower tile only adds MMA issues (an M = 128 MMA costs ~55 cycles
+        // at N <= 64, 64 at N = 128): they run 64 complex columns wide (or the whole radix)
+        // whatever the tuned width. (The 48-column mode-product tiles have stages and a hold
+        // sized for 48 columns and keep their width.)
         const int rad = a.bnc * a.ncol_tiles;
         const int wide = rad < 64 ? rad : 64;
         a.num_tiles = a.num_tiles / a.ncol_tiles * (rad / wide);
