@@ -1581,6 +1581,12 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
                                 const uint32_t* __restrict__ prefixes, int64_t npre,
                                 uint32_t* __restrict__ planes, int64_t plane_stride_u32)
 {
+    // the rank table (rows 0..N of C(n - v + r - 1, r), <= 5 x 129 entries) in shared memory:
+    // every gathered record's rank reads it, and from global memory its dependent loads made
+    // the kernel latency-bound
+    __shared__ int64_t s_cnt[5 * (NP + 1)];
+    for (int t = threadIdx.x; t < (N + 1) * (n + 1); t += blockDim.x) s_cnt[t] = cnt[t];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1608,7 +1614,7 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
                     a[k++] = pre[m];
                 }
                 if (!placed) a[k++] = aN;
-                const int64_t q = tuple_rank(a, N, cnt, n);
+                const int64_t q = tuple_rank(a, N, s_cnt, n);
                 const uint4 r0 = rec[((int64_t)(i0 + il) * P + q) * 2 + 0];
                 const uint4 r1 = rec[((int64_t)(i0 + il) * P + q) * 2 + 1];
                 const uint32_t rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
