@@ -6,6 +6,7 @@ CPU-baseline leg may import this package; the library never does.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -21,16 +22,42 @@ _lock = threading.Lock()
 _lib = None
 
 
+_CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fcx-limited-range",
+           "-fno-fast-math"]
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile a C source of the oracle's interface with the oracle's own flags into `out`."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *_CFLAGS, "-o", tmp, src, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile npf_oracle.c with gcc (-O2, OpenMP, no fast-math) into oracle/_build/."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fcx-limited-range",
-               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
+        compile_source(_SRC, _SO)
     return _SO
+
+
+def _bind(lib):
+    i64 = ctypes.c_int64
+    ci = ctypes.c_int
+    cdbl = ctypes.c_double
+    vp = ctypes.c_void_p
+    lib.npfo_packed_count.restype = i64
+    lib.npfo_packed_count.argtypes = [ci, ci]
+    lib.npfo_unpack.argtypes = [ci, ci, vp, vp]
+    lib.npfo_h_brute.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, vp]
+    lib.npfo_psiN_brute.argtypes = [ci, ci, vp, vp, vp]
+    lib.npfo_h_fact.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, ci, ci, vp]
+    lib.npfo_psiN_accumulate.argtypes = [ci, ci, vp, vp, ci, ci, vp]
+    lib.npfo_psiN.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, ci, vp]
+    lib.npfo_h_slab.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, vp, vp]
+    lib.npfo_npf.argtypes = [ci, vp, vp, vp, vp]
+    return lib
 
 
 def _load():
@@ -38,23 +65,23 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_SO)
-            i64 = ctypes.c_int64
-            ci = ctypes.c_int
-            cdbl = ctypes.c_double
-            vp = ctypes.c_void_p
-            lib.npfo_packed_count.restype = i64
-            lib.npfo_packed_count.argtypes = [ci, ci]
-            lib.npfo_unpack.argtypes = [ci, ci, vp, vp]
-            lib.npfo_h_brute.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, vp]
-            lib.npfo_psiN_brute.argtypes = [ci, ci, vp, vp, vp]
-            lib.npfo_h_fact.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, ci, ci, vp]
-            lib.npfo_psiN_accumulate.argtypes = [ci, ci, vp, vp, ci, ci, vp]
-            lib.npfo_psiN.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, ci, vp]
-            lib.npfo_h_slab.argtypes = [ci, ci, vp, vp, vp, vp, cdbl, ci, vp, vp]
-            lib.npfo_npf.argtypes = [ci, vp, vp, vp, vp]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_SO))
     return _lib
+
+
+@contextlib.contextmanager
+def substituted_library(so_path: str):
+    """Run the oracle's functions on another compiled copy of its C source (a test that plants
+    a mistake in the oracle checks that the pins catch it); the own library is restored after."""
+    global _lib
+    own = _load()
+    with _lock:
+        _lib = _bind(ctypes.CDLL(os.path.abspath(so_path)))
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = own
 
 
 def _f64(a):

@@ -189,12 +189,23 @@ def test_eps_clamp_is_strict_and_real():
     h = oracle.h_fact(pk, n, N, I, I, lam, eps=eps)
     np.testing.assert_allclose(h[2, 0, 1], 3.0 / (2 * eps), rtol=1e-14)
     np.testing.assert_allclose(h[2, 1, 0], 3.0 / (2 * eps), rtol=1e-14)
-    # exactly at eps the clamp does not fire (strict <)
+    # just above eps the clamp does not fire
     lam2 = lam.copy()
     lam2[2] = lam[0] + lam[1] - 2e-8
     h2 = oracle.h_fact(pk, n, N, I, I, lam2, eps=eps)
     D = lam2[0] + lam2[1] - lam2[2]
     np.testing.assert_allclose(h2[2, 0, 1], 3.0 / (2 * D), rtol=1e-6)
+    # exactly at eps it does not fire either (strict <): D = (3 + 4i) 2^-28, |D| = 5 * 2^-28, with
+    # every sum exact, so a clamp that fired would turn the complex D into the real eps
+    Dx = (3 + 4j) * 2.0 ** -28
+    lam3 = lam.copy()
+    lam3[2] = complex(-1.5 - 3 * 2.0 ** -28, 3 - 4 * 2.0 ** -28)
+    assert (-lam3[2] + lam3[0]) + lam3[1] == Dx
+    eps3 = 5 * 2.0 ** -28
+    if abs(Dx) != eps3:
+        pytest.skip("this libm's hypot does not return 5 * 2^-28 exactly for (3, 4) * 2^-28")
+    h3 = oracle.h_fact(pk, n, N, I, I, lam3, eps=eps3)
+    np.testing.assert_allclose(h3[2, 0, 1], 3.0 / (2 * Dx), rtol=1e-14)
 
 
 @pytest.mark.parametrize("n,N", [(4, 2), (6, 2), (4, 3), (6, 3), (4, 4), (6, 4)])
