@@ -6,14 +6,21 @@ conjugated quotient, a wrong Khatri-Rao orientation, a lost minus sign, an off-b
 clamp that is not strict or not real, ...). It is compiled with the oracle's own flags and every
 pin of test_oracle_pins runs on it through oracle.substituted_library; the unchanged source,
 compiled the same way, passes them all. No mutant reads or writes outside its arrays.
+
+The oracle's Python parts (the mode-interaction NPFs of Eqs. 6-9, the mode subset, the swing-model
+tensors and the surrogate network) get the same treatment: a copy of the module's source with one
+mistake is executed as a fresh module and the pins of that module run against it.
 """
 import concurrent.futures
+import contextlib
 import os
+import types
 
 import pytest
 
 import oracle
-from tests import test_oracle_pins as pins
+from tests import test_oracle_interaction, test_oracle_mlp, test_oracle_pins as pins
+from tests import test_oracle_subset, test_oracle_swing
 
 # (name, text in npf_oracle.c (exactly once), replacement)
 MUTANTS = [
@@ -125,3 +132,98 @@ def test_unchanged_source_passes_every_pin(compiled):
 def test_planted_mistake_is_caught(compiled, name):
     failed = _failing_pins(compiled[name])
     assert failed, f"no pin catches: {name}"
+
+
+_ORACLE_DIR = os.path.dirname(oracle._SRC)
+# module file -> [(test module, the name under which it holds the oracle module)]
+PY_PINS = {
+    "__init__.py": [(test_oracle_interaction, "oracle"), (test_oracle_subset, "oracle")],
+    "swing.py": [(test_oracle_swing, "swing")],
+    "mlp.py": [(test_oracle_mlp, "M")],
+}
+# (name, module file, text (exactly once), replacement)
+PY_MUTANTS = [
+    ("Eq. 7 correction of z(0) with the wrong sign", "__init__.py",
+     "z = z + delta ** N * psiN(", "z = z - delta ** N * psiN("),
+    ("Eq. 7 correction with delta^(N-1)", "__init__.py",
+     "z = z + delta ** N * psiN(", "z = z + delta ** (N - 1) * psiN("),
+    ("pN1 with phi_ik for phi_ki", "__init__.py", "out[0] = U * z.T", "out[0] = U * z"),
+    ("Eqs. 8-9 with zeta in place of the corrected z(0)", "__init__.py",
+     "reduce_weights(sysm.tensors[M], n, M, U, V, sysm.lam, z, eps, True, p1_block)",
+     "reduce_weights(sysm.tensors[M], n, M, U, V, sysm.lam, delta * V, eps, True, p1_block)"),
+    ("weighted contraction without its minus sign", "__init__.py", "    return -acc\n",
+     "    return acc\n"),
+    ("subset: weights of every mode", "__init__.py", "W[modes] = _c128(V)[modes]",
+     "W[:] = _c128(V)"),
+    ("subset: rows of every mode", "__init__.py", "out[modes] = -T[modes]", "out[:] = -T"),
+    ("swing: no quarter-turn phase per derivative", "swing.py",
+     "return G * math.cos(t + N * math.pi / 2) + B * math.sin(t + N * math.pi / 2)",
+     "return G * math.cos(t + (N - 1) * math.pi / 2) + B * math.sin(t + (N - 1) * math.pi / 2)"),
+    ("swing: sign of the derivatives in delta_k", "swing.py", "(-1) ** b", "(-1) ** a"),
+    ("swing: network coefficient without its minus sign", "swing.py",
+     "coef = -model.V[j] / (2.0 * model.H[j])", "coef = model.V[j] / (2.0 * model.H[j])"),
+    ("swing: reference-bus line dropped", "swing.py",
+     "total += _gN(model.Gb[j], model.Bb[j], model.delta[j], N)", "total += 0.0"),
+    ("network: relu derivative dropped", "mlp.py", "dz = _q((dz @ W) * (h > 0.0), bf16)",
+     "dz = _q(dz @ W, bf16)"),
+    ("network: loss derivative without its factor 2", "mlp.py",
+     "dz = _q(2.0 * d / (R * wo), bf16)", "dz = _q(d / (R * wo), bf16)"),
+    ("network: bias column left out of the gradient", "mlp.py",
+     "ha = np.concatenate([h, np.ones((R, 1))], axis=1)",
+     "ha = np.concatenate([h, np.zeros((R, 1))], axis=1)"),
+    ("bfloat16 rounding by truncation", "mlp.py",
+     "r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)",
+     "r = (u >> np.uint64(16)) << np.uint64(16)"),
+    ("bfloat16 ties rounded away from zero", "mlp.py",
+     "r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)",
+     "r = ((u + np.uint64(0x8000)) >> np.uint64(16)) << np.uint64(16)"),
+]
+
+
+def _module_from(fname, text):
+    path = os.path.join(_ORACLE_DIR, fname)
+    mod = types.ModuleType(f"oracle_copy_{fname[:-3]}")
+    mod.__file__ = path
+    exec(compile(text, path, "exec"), mod.__dict__)
+    return mod
+
+
+@contextlib.contextmanager
+def _held_by(targets, mod):
+    old = [(t, attr, getattr(t, attr)) for t, attr in targets]
+    try:
+        for t, attr in targets:
+            setattr(t, attr, mod)
+        yield
+    finally:
+        for t, attr, v in old:
+            setattr(t, attr, v)
+
+
+def _failing_py_pins(fname, text):
+    mod = _module_from(fname, text)
+    failed = []
+    with _held_by(PY_PINS[fname], mod):
+        for tmod, _ in PY_PINS[fname]:
+            for name in sorted(dir(tmod)):
+                if name.startswith("test_"):
+                    try:
+                        getattr(tmod, name)()
+                    except pytest.skip.Exception:
+                        pass
+                    except Exception:
+                        failed.append(f"{tmod.__name__}.{name}")
+    return failed
+
+
+@pytest.mark.parametrize("fname", sorted(PY_PINS))
+def test_unchanged_python_module_passes_its_pins(fname):
+    text = open(os.path.join(_ORACLE_DIR, fname)).read()
+    assert _failing_py_pins(fname, text) == []
+
+
+@pytest.mark.parametrize("name,fname,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_planted_python_mistake_is_caught(name, fname, old, new):
+    text = open(os.path.join(_ORACLE_DIR, fname)).read()
+    assert text.count(old) == 1, (name, text.count(old))
+    assert _failing_py_pins(fname, text.replace(old, new)), f"no pin catches: {name}"
