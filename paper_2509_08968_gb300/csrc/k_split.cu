@@ -1554,19 +1554,6 @@ __global__ void k_s_records(const double2* __restrict__ Sd, int64_t ld, int64_t 
     }
 }
 
-// Next distinct ordering of v[0..len-1] in lexicographic order (false after the last one).
-__device__ __forceinline__ bool next_ordering(int* v, int len)
-{
-    int k = len - 2;
-    while (k >= 0 && v[k] >= v[k + 1]) --k;
-    if (k < 0) return false;
-    int l = len - 1;
-    while (v[l] <= v[k]) --l;
-    const int t = v[k]; v[k] = v[l]; v[l] = t;
-    for (int a = k + 1, b = len - 1; a < b; ++a, --b) { const int u = v[a]; v[a] = v[b]; v[b] = u; }
-    return true;
-}
-
 // Dense expansion by sorted row prefix: one warp per (upper index i, non-decreasing prefix
 // (a_1..a_{N-1}) over [0, n)). Lane t covers a_N = lane + 32 t. The 128 K' digit records
 // S^i_{sort(prefix, a_N)} are gathered once and written to every distinct ordering of the
@@ -1599,44 +1586,76 @@ __global__ void k_expand_sorted(const uint4* __restrict__ rec, int64_t P, int n,
         int pre[3];
 #pragma unroll
         for (int m = 0; m < 3; ++m) pre[m] = (int)((pk >> (8 * m)) & 255u);
-        uint32_t w[4][S];
+        // The four records' ranks first, then their eight loads back to back, so that a lane's
+        // gathers are in flight together. The sorted tuple is the prefix with a_N inserted at
+        // pos (the number of prefix values <= a_N); its rank is the telescoped count over the
+        // tuple, with every index a compile-time constant so that nothing goes to local memory.
+        int64_t qv[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int aN = lane + 32 * t;
-#pragma unroll
-            for (int s = 0; s < S; ++s) w[t][s] = 0u;
+            qv[t] = -1;
             if (aN < n) {
-                int a[4];
-                int k = 0;
-                bool placed = false;
-                for (int m = 0; m < nd; ++m) {
-                    if (!placed && aN < pre[m]) { a[k++] = aN; placed = true; }
-                    a[k++] = pre[m];
-                }
-                if (!placed) a[k++] = aN;
-                const int64_t q = tuple_rank(a, N, s_cnt, n);
-                const uint4 r0 = rec[((int64_t)(i0 + il) * P + q) * 2 + 0];
-                const uint4 r1 = rec[((int64_t)(i0 + il) * P + q) * 2 + 1];
-                const uint32_t rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                int pos = 0;
 #pragma unroll
-                for (int s = 0; s < S; ++s) w[t][s] = rr[s];
+                for (int m = 0; m < 3; ++m) pos += (m < nd && pre[m] <= aN) ? 1 : 0;
+                int64_t r = 0;
+                int prev = 0;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (m < N) {
+                        const int sm = m < pos ? pre[m < 3 ? m : 2]
+                                               : (m == pos ? aN : pre[m >= 1 ? m - 1 : 0]);
+                        const int64_t* row = s_cnt + (N - m) * (n + 1);
+                        r += row[prev] - row[sm];
+                        prev = sm;
+                    }
+                }
+                qv[t] = r;
             }
         }
-        int ord[3] = {pre[0], pre[1], pre[2]};
-        do {
-            // the first contraction only runs rows whose shared indices are non-decreasing
-            bool sorted_shared = true;
-            for (int m = 1; m < nd - 1; ++m) sorted_shared &= ord[m - 1] <= ord[m];
-            if (!sorted_shared) continue;
-            int64_t row = 0;
-            for (int m = 0; m < nd; ++m) row = (row << lg) + ord[m];
+        uint4 r0[4], r1[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            r0[t] = make_uint4(0u, 0u, 0u, 0u);
+            r1[t] = make_uint4(0u, 0u, 0u, 0u);
+            if (qv[t] >= 0) {
+                r0[t] = rec[((int64_t)(i0 + il) * P + qv[t]) * 2 + 0];
+                r1[t] = rec[((int64_t)(i0 + il) * P + qv[t]) * 2 + 1];
+            }
+        }
+        uint32_t w[4][S];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t rr[8] = {r0[t].x, r0[t].y, r0[t].z, r0[t].w, r1[t].x, r1[t].y, r1[t].z, r1[t].w};
+#pragma unroll
+            for (int s = 0; s < S; ++s) w[t][s] = rr[s];
+        }
+        // every distinct ordering of the prefix whose shared indices (all but the last) are
+        // non-decreasing, which is what the first contraction runs: for x <= y <= z these are
+        // (x, y, z), (x, z, y) when y < z and (y, z, x) when x < y; (x, y) and (y, x) when x < y
+        auto write_row = [&](int o0, int o1, int o2) {
+            int64_t row = o0;
+            if (nd >= 2) row = (row << lg) + o1;
+            if (nd >= 3) row = (row << lg) + o2;
             uint32_t* dst = planes + (((int64_t)il * rows_per_i + row) << lg) + lane;
 #pragma unroll
             for (int t = 0; t < 4; ++t)
                 if (32 * t < kw)
 #pragma unroll
                     for (int s = 0; s < S; ++s) dst[s * plane_stride_u32 + 32 * t] = w[t][s];
-        } while (next_ordering(ord, nd));
+        };
+        const int x = pre[0], y = pre[1], z = pre[2];
+        if (nd <= 1) {   // (order 1: one empty prefix, row 0)
+            write_row(x, 0, 0);
+        } else if (nd == 2) {
+            write_row(x, y, 0);
+            if (x != y) write_row(y, x, 0);
+        } else {
+            write_row(x, y, z);
+            if (y != z) write_row(x, z, y);
+            if (x != y) write_row(y, z, x);
+        }
     }
 }
 
